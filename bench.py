@@ -1,0 +1,385 @@
+"""Throughput of batched Boys-function evaluation on GB300 (one JSON line).
+
+Workload (one step): FP64 stored mode at kmax = 32 over N = 2^26 arguments
+drawn from the ERI-shaped mixture (40% log-uniform [1e-12, 1e2], 40% uniform
+[0, 60], 20% uniform [60, 1e4]); output F_0..F_32 order-major [33][N]
+(17.7 GB).  Metric: F_k values per second = N * 33 / step time.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+* ``value``     device-resident inputs, CUDA-event timing of K steps on the
+                launching stream, barrier + synchronize on both sides, max
+                over ranks; every rank evaluates its own 2^26 arguments (weak
+                scaling, no data-path collective).
+* ``e2e``       the same metric through the public API with host buffers:
+                each step copies x from pinned host memory, evaluates, and
+                copies all of F back to pinned host memory.
+* ``roofline``  the dominant kernel (the FP64 evaluation kernel) against its
+                binding roof: algorithmic FP64 flops (FMA = 2, each divide /
+                exp / rsqrt = 1) over the FP64 peak, or algorithmic HBM bytes
+                (8 + 8*33 per argument) over the measured copy bandwidth,
+                whichever roof takes longer.
+* ``cpu_baseline`` the binary128 oracle on the host cores, on a bounded
+                sample of the same workload.
+``--impl reference`` times that oracle alone (rank 0 only) and prints its line.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "F_k values/s at kmax=32: FP64 (≤5e-14) vs FP32 tier (≤1e-6); % of roofline"
+UNIT = "F_k values/s"
+KMAX = 32
+N_PER_GPU = 1 << 26
+WORKLOAD = "boys_fp64_stored_kmax32_n2^26_eri_mixture"
+
+# FP64 peak: the recipe's nominal 1.25 TFLOP/s for GB300 is 152 SMs x 2 DFMA per
+# clock per SM x 2 flop x 2.07 GHz = 1.259 TFLOP/s (an in-house DFMA loop measured
+# 1.19 TFLOP/s, 95% of it).  Burst HBM copy bandwidth is driver-measured.
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+HBM_FALLBACK_GBS = 6800.0
+# DRAM bytes per argument of the timed kernel from an ncu capture (profiles/);
+# None until a capture of the current kernel exists.
+TRAFFIC_BYTES_PER_X = None
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return HBM_FALLBACK_GBS, "fallback"
+
+
+def flops_per_x(x, kmax):
+    """Algorithmic FP64 flops per argument, by region (FMA = 2; divide, exp,
+    rsqrt = 1 each), summed over the actual region membership of x."""
+    from paper_2512_10059_gb300 import workloads as W
+    na, ma = RA_DEGREES[kmax]
+    a = 2 * (na + ma) + 2 + 3 * kmax           # Horner P,Q + divide + exp + kmax (FMA + MUL)
+    b = 2 * (5 + 6) + 4 + 3 * kmax             # Horner r_B + divide + exp + 2x + 1/(2x) + steps
+    c = 2 + 2 * kmax                           # rsqrt + 1/x + kmax * 2 MUL
+    inA = x < W.X0_PRINTED
+    inC = x >= W.X1_PRINTED
+    nA = int(np.count_nonzero(inA))
+    nC = int(np.count_nonzero(inC))
+    nB = x.size - nA - nC
+    return (a * nA + b * nB + c * nC) / x.size, (nA / x.size, nB / x.size, nC / x.size)
+
+
+# (n, m) of r_{A,k}, Appendix D
+RA_DEGREES = [(6, 9), (6, 10), (6, 10), (4, 12), (8, 9), (4, 13), (8, 9), (4, 13), (8, 9), (8, 9),
+              (8, 9), (8, 9), (8, 9), (8, 9), (8, 9), (8, 9), (8, 9), (8, 9), (8, 8), (8, 8), (7, 9),
+              (8, 8), (8, 8), (8, 8), (8, 8), (8, 8), (7, 8), (7, 8), (7, 8), (7, 8), (7, 8), (7, 8),
+              (7, 8)]
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clock and throttle reasons during a region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id):
+        self.gpu = gpu_id
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        try:
+            for ln in open(self.path):
+                parts = [p.strip() for p in ln.split(",")]
+                if len(parts) >= 9 and parts[1].replace(".", "").isdigit():
+                    rows.append(parts)
+        finally:
+            try:
+                os.unlink(self.path)
+            except OSError:
+                pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        sm = [float(r[1]) for r in rows]
+        pw = [float(r[3]) for r in rows if r[3].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[j] for r in rows for j in range(4) if r[5 + j].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": float(rows[0][2]), "reasons": reasons,
+                "samples": len(rows), "power_w_max": max(pw) if pw else None}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def oracle_sample_rate(kmax, seconds=12.0, threads=0, start=0):
+    """The binary128 oracle on host cores over consecutive chunks of the same
+    workload until ~`seconds` of wall time; returns (values/s, x evaluated)."""
+    import oracle
+    from paper_2512_10059_gb300 import workloads as W
+    chunk = 2048
+    done = 0
+    t0 = time.perf_counter()
+    pool = W.mixture_c2(1 << 18, seed=1)
+    while time.perf_counter() - t0 < seconds and done + chunk <= pool.size:
+        oracle.boys(pool[done:done + chunk], kmax, nthreads=threads)
+        done += chunk
+    dt = time.perf_counter() - t0
+    return done * (kmax + 1) / dt, done, dt
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+    threads = oracle.max_threads()
+    for _ in range(args.warmup):
+        oracle_sample_rate(KMAX, seconds=0.5)
+    step_s = args.ref_step_seconds or min(5.0, 150.0 / max(1, args.steps))
+    rates, xs, secs = [], 0, 0.0
+    for _ in range(args.steps):
+        r, n, dt = oracle_sample_rate(KMAX, seconds=step_s)
+        rates.append(r)
+        xs += n
+        secs += dt
+    value = xs * (KMAX + 1) / secs
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f128",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "kmax": KMAX, "n": N_PER_GPU,
+                   "reference": "binary128 CPU oracle (oracle/boys_oracle.c), bounded samples of the workload"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": f"{xs} arguments of the same mixture in 2048-argument chunks, "
+                                   f"~{step_s:.1f} s per step"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def run_ours(args):
+    import torch
+    ws, rank, local = dist_env()
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    import paper_2512_10059_gb300 as pb
+    from paper_2512_10059_gb300 import _lib
+    from paper_2512_10059_gb300 import workloads as W
+
+    n = 1 << args.n_log2
+    # each rank owns elements [rank*n, (rank+1)*n) of the global argument stream
+    x_host = W.mixture_c2(n, seed=1 + 1000 * rank) if rank else W.mixture_c2(n, seed=1)
+    fpx, fracs = flops_per_x(x_host, KMAX)
+    x = torch.from_numpy(x_host).to(dev)
+    out = torch.empty((KMAX + 1, n), dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    L = _lib.lib()
+    hs = int(stream.cuda_stream)
+
+    def step():
+        st = L.boys_eval(x.data_ptr(), n, KMAX, out.data_ptr(), n, hs)
+        if st != 0:
+            _lib.check("boys_eval", st)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    for _ in range(args.warmup):
+        step()
+    barrier()
+
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    props = torch.cuda.get_device_properties(dev)
+    smi_id = f"GPU-{props.uuid}" if getattr(props, "uuid", None) else str(local)
+    with ClockSampler(smi_id) as clk:
+        barrier()
+        t_start.record(stream)
+        for e0, e1 in evs:
+            e0.record(stream)
+            step()
+            e1.record(stream)
+        t_end.record(stream)
+        torch.cuda.synchronize(dev)
+        barrier()
+    clocks = clk.summary()
+    total_ms = t_start.elapsed_time(t_end)
+    launch_ms = [a.elapsed_time(b) for a, b in evs]
+    total_t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+    if dist is not None:
+        dist.all_reduce(total_t, op=dist.ReduceOp.MAX)
+    total_ms = float(total_t.item())
+    ms_per_step = total_ms / args.steps
+    value = ws * n * (KMAX + 1) * args.steps / (total_ms / 1e3)
+
+    # roofline of the evaluation kernel
+    hbm_gbs, hbm_src = peaks()
+    avg_launch_s = statistics.mean(launch_ms) / 1e3
+    bytes_per_launch = n * 8 * (KMAX + 2)
+    flops_per_launch = n * fpx
+    t_hbm = bytes_per_launch / (hbm_gbs * 1e9)
+    t_fp64 = flops_per_launch / (FP64_PEAK_TFLOPS * 1e12)
+    if t_fp64 >= t_hbm:
+        roof = {"bound": "alu", "achieved": flops_per_launch / avg_launch_s / 1e12, "peak": FP64_PEAK_TFLOPS,
+                "unit": "TFLOP/s", "peak_source": "FP64 nominal: 152 SM x 2 DFMA/clk x 2 flop x 2.07 GHz"}
+    else:
+        roof = {"bound": "hbm", "achieved": bytes_per_launch / avg_launch_s / 1e9, "peak": hbm_gbs,
+                "unit": "GB/s", "peak_source": f"{hbm_src} copy bandwidth"}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["traffic"] = None if TRAFFIC_BYTES_PER_X is None else TRAFFIC_BYTES_PER_X * n
+    roof["kernel"] = "k_eval_f64<32,2>"
+    roof["algorithmic_flops_per_x"] = fpx
+    roof["algorithmic_bytes_per_x"] = 8 * (KMAX + 2)
+    roof["hbm_frac"] = bytes_per_launch / avg_launch_s / 1e9 / hbm_gbs
+    roof["fp64_frac"] = flops_per_launch / avg_launch_s / 1e12 / FP64_PEAK_TFLOPS
+
+    # fused consumer on the same arguments (one extra input rho, one output per x)
+    fused = None
+    if not args.skip_modes:
+        rho = torch.from_numpy(W.rho_c2(n, seed=2)).to(dev)
+        fout = torch.empty(n, dtype=torch.float64, device=dev)
+        for _ in range(args.warmup):
+            pb.boys_eval_fused(x, rho, KMAX, out=fout)
+        barrier()
+        f0 = torch.cuda.Event(enable_timing=True)
+        f1 = torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        for _ in range(args.steps):
+            pb.boys_eval_fused(x, rho, KMAX, out=fout)
+        f1.record(stream)
+        torch.cuda.synchronize(dev)
+        fms = f0.elapsed_time(f1) / args.steps
+        ffl = n * (fpx + 2 * KMAX + 1)
+        fused = {"value": n * (KMAX + 1) / (fms / 1e3), "unit": UNIT, "ms_per_step": fms,
+                 "fp64_tflops": ffl / (fms / 1e3) / 1e12,
+                 "fp64_frac": ffl / (fms / 1e3) / 1e12 / FP64_PEAK_TFLOPS,
+                 "hbm_gbs": n * 24 / (fms / 1e3) / 1e9}
+        del rho, fout
+
+    # end to end through the public API with pinned host buffers
+    e2e = None
+    if not args.skip_e2e:
+        xh = torch.from_numpy(x_host).pin_memory()
+        oh = torch.empty((KMAX + 1, n), dtype=torch.float64, pin_memory=True)
+
+        def e2e_step():
+            x.copy_(xh, non_blocking=True)
+            pb.boys_eval(x, KMAX, out=out)
+            oh.copy_(out, non_blocking=True)
+
+        for _ in range(2):
+            e2e_step()
+        barrier()
+        k_e2e = max(2, min(args.steps, 5))
+        g0 = torch.cuda.Event(enable_timing=True)
+        g1 = torch.cuda.Event(enable_timing=True)
+        g0.record(stream)
+        for _ in range(k_e2e):
+            e2e_step()
+        g1.record(stream)
+        torch.cuda.synchronize(dev)
+        barrier()
+        ems = torch.tensor([g0.elapsed_time(g1)], dtype=torch.float64, device=dev)
+        if dist is not None:
+            dist.all_reduce(ems, op=dist.ReduceOp.MAX)
+        ems = float(ems.item())
+        e2e = {"value": ws * n * (KMAX + 1) * k_e2e / (ems / 1e3), "unit": UNIT,
+               "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": 8 * (KMAX + 1) * n,
+               "ms_per_step": ems / k_e2e, "steps": k_e2e}
+        del xh, oh
+
+    cpu = None
+    if rank == 0 and not args.skip_cpu:
+        import oracle
+        r, xs, dt = oracle_sample_rate(KMAX, seconds=args.cpu_seconds)
+        cpu = {"value": r, "unit": UNIT, "cores": oracle.max_threads(), "kind": "oracle",
+               "sample": f"{xs} arguments of the same mixture (binary128, {dt:.1f} s wall)"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD if args.n_log2 == 26 else f"{WORKLOAD}_profiling_n2^{args.n_log2}",
+                       "kmax": KMAX, "n_per_gpu": n, "output": "order-major [33][N] FP64",
+                       "region_fractions_ABC": [round(f, 4) for f in fracs],
+                       "l2": "inputs larger than L2 (x 0.54 GB read, 17.7 GB written per step); no flush",
+                       "parallelism": f"replicas x{ws}, no data-path collective"},
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": args.steps,
+            "clocks": clocks, "modes": {"fused_kmax32": fused},
+        }
+        print(json.dumps(line))
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--ref-step-seconds", type=float, default=None)
+    ap.add_argument("--n-log2", type=int, default=26,
+                    help="arguments per GPU = 2^n (26 is the benchmarked workload; smaller only for profiling)")
+    ap.add_argument("--skip-e2e", action="store_true")
+    ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--skip-modes", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,90 @@
+/*
+ * libboys — batched Boys-function evaluation on NVIDIA GB300 (sm_103a).
+ *
+ * Implements the evaluation algorithm of Vikhamar-Sandberg & Repisky,
+ * "Efficient Boys function evaluation using minimax approximation"
+ * (arXiv:2512.10059): Section II.C / Eq. 3 define
+ *     F_k(x) = \int_0^1 t^{2k} e^{-x t^2} dt,  x >= 0,
+ * and Algorithm 1 evaluates F_0..F_kmax by splitting [0, inf) into
+ *     A = [0, x_0)   rational minimax anchor r_{A,kmax}, downward recurrence
+ *     B = [x_0, x_1) rational minimax r_B for F_0, upward recurrence
+ *     C = [x_1, inf) asymptotic F_0 = sqrt(pi)/2 x^{-1/2}, upward recurrence
+ * with x_0, x_1 and all FP64 coefficients from the paper's Appendix D
+ * (eps_tol = 5e-14 absolute for every order k <= 32).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  * Array pointers are DEVICE pointers (CUDA global memory) owned by the
+ *    caller; the library never frees or retains them beyond the call.
+ *  * `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Every compute entry point only enqueues work on it and
+ *    returns; results are ready when the stream reaches that point.
+ *  * Output layout is order-major ("SoA"): F_k(x_i) is stored at
+ *    out[k * ld + i], 0 <= k <= kmax, 0 <= i < n, with ld >= n.  Offsets
+ *    are 64-bit.
+ *  * Argument errors are reported synchronously by the return value and
+ *    enqueue nothing.  n == 0 is a no-op that returns BOYS_OK.
+ *  * Domain conventions (the paper defines x >= 0 only): x < 0 or NaN
+ *    gives NaN for every order; x = +inf gives 0; -0.0 is treated as 0.
+ *    These are not errors (detecting them would need a synchronisation).
+ *  * Launch failures return BOYS_ERR_CUDA; boys_last_error() then holds
+ *    the CUDA error text for the calling thread.
+ */
+#ifndef LIBBOYS_BOYS_H
+#define LIBBOYS_BOYS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum boys_status {
+    BOYS_OK = 0,
+    BOYS_ERR_INVALID_ARG = 1, /* NULL pointer, n < 0, ld < n, size overflow  */
+    BOYS_ERR_KMAX = 2,        /* kmax outside the range the entry point supports */
+    BOYS_ERR_ALIGNMENT = 3,   /* pointer not aligned to its element size      */
+    BOYS_ERR_CUDA = 4         /* a CUDA runtime call or launch failed          */
+} boys_status;
+
+/* Human-readable name of a status code (static string, never NULL). */
+const char* boys_status_string(int status);
+
+/* Text of the last BOYS_ERR_* raised on the calling thread ("" if none). */
+const char* boys_last_error(void);
+
+/* Library version as major*10000 + minor*100 + patch. */
+int boys_version(void);
+
+/* Highest kmax accepted by the FP64 entry points (32, the paper's table set). */
+int boys_kmax_limit(void);
+
+/*
+ * FP64 stored mode — Algorithm 1 for every x_i.
+ *   x    [n]            input arguments (8-byte aligned; 16-byte alignment
+ *                       of x, out and an even ld enable 128-bit accesses)
+ *   n                   number of arguments, n >= 0
+ *   kmax                highest order, 0 <= kmax <= 32
+ *   out  [kmax+1][ld]   F_k(x_i) at out[k*ld + i]; ld >= n
+ * Accuracy: |F_k - exact| <= 5e-14 absolute for every k (the paper's
+ * eps_tol; at x = x_1 exactly the asymptotic form's own error exceeds it by
+ * ~1e-29, see the design notes).  Results are bitwise deterministic.
+ */
+boys_status boys_eval(const double* x, int64_t n, int kmax, double* out, int64_t ld,
+                      void* stream);
+
+/*
+ * FP64 fused consumer — the F_k never leave registers:
+ *   out[i] = sum_{k=0}^{kmax} (-2 rho_i)^k F_k(x_i)
+ * (the McMurchie-Davidson-style scaling of an electron-repulsion-integral
+ * kernel; the F_k are evaluated exactly as boys_eval does).
+ *   x, rho [n] inputs; out [n] output; 0 <= kmax <= 32.
+ */
+boys_status boys_eval_fused(const double* x, const double* rho, int64_t n, int kmax,
+                            double* out, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LIBBOYS_BOYS_H */

@@ -1,0 +1,165 @@
+"""FP64 stored and fused modes through the C ABI against the binary128 oracle.
+
+Tolerance: the paper's eps_tol = 5e-14 absolute for every order (abstract,
+Section I), plus 1e-27 round-off slack at x = x_1 exactly, where Eq. x1 is
+tight (the asymptotic error of F_32 there is 5e-14 + ~1e-29).
+Fused tolerance: the F_k errors propagate as sum_k (2 rho)^k * 5e-14, plus
+the Horner sum's own rounding, 64 * 2^-53 * sum_k |(2 rho)^k F_k|.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_2512_10059_gb300 as pb
+from paper_2512_10059_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+EPS = 5e-14
+SLACK = 1e-27
+DEV = "cuda:0"
+
+
+def _err(got, hi, lo):
+    return np.abs((got - hi) - lo)
+
+
+def _check(x, got, kmax, what=""):
+    hi, lo = oracle.boys(x, kmax)
+    nan_ref = np.isnan(hi)
+    assert np.array_equal(np.isnan(got), nan_ref), f"{what}: NaN pattern differs"
+    err = np.where(nan_ref, 0.0, _err(got, hi, lo))
+    worst = err.max() if err.size else 0.0
+    if worst > EPS + SLACK:
+        k, i = np.unravel_index(err.argmax(), err.shape)
+        raise AssertionError(f"{what}: max abs err {worst:.3e} at k={k} x={x[i]!r}")
+    return err
+
+
+def _eval(x, kmax):
+    xt = torch.from_numpy(np.ascontiguousarray(x)).to(DEV)
+    out = pb.boys_eval(xt, kmax)
+    torch.cuda.synchronize()
+    return out.cpu().numpy()
+
+
+def test_c1_every_point():
+    """The kmax = 8 parity mixture, all 65536 arguments (zeros, boundary
+    neighbourhoods, log-uniform bulk)."""
+    x = W.mixture_c1(65536, seed=0)
+    _check(x, _eval(x, 8), 8, "c1")
+
+
+@pytest.mark.parametrize("kmax", list(range(33)))
+def test_every_kmax(kmax):
+    x = np.concatenate([W.small_parity_set(), W.mixture_c1(3000, seed=100 + kmax),
+                        np.linspace(0.0, 40.0, 2001)])
+    _check(x, _eval(x, kmax), kmax, f"kmax={kmax}")
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 31, 32, 33, 255, 256, 257, 1023, 4097, 40961])
+def test_sizes_and_ragged_tails(n):
+    x = W.mixture_c2(n, seed=9)
+    _check(x, _eval(x, 11), 11, f"n={n}")
+
+
+def test_unaligned_and_strided_layouts():
+    x = W.mixture_c1(5001, seed=21)
+    base = torch.from_numpy(np.concatenate([[0.0], x])).to(DEV)
+    xv = base[1:]                       # 8-byte but not 16-byte aligned: scalar path
+    buf = torch.full((9, 5003), -7.0, dtype=torch.float64, device=DEV)
+    out = buf[:, :5001]                 # ld = 5003 (odd): scalar stores
+    pb.boys_eval(xv, 8, out=out)
+    ref_vec = pb.boys_eval(torch.from_numpy(x).to(DEV), 8)
+    torch.cuda.synchronize()
+    got = out.cpu().numpy()
+    _check(x, got, 8, "unaligned")
+    assert np.array_equal(got, ref_vec.cpu().numpy()), "scalar and 128-bit paths differ bitwise"
+    assert torch.all(buf[:, 5001:] == -7.0), "wrote outside [0, n) of a row"
+
+
+def test_special_values():
+    x = np.array([np.nan, -1.0, -1e-300, np.inf, -0.0, 0.0, 5e-324, 1.7e308, W.X0_PRINTED, W.X1_PRINTED])
+    got = _eval(x, 32)
+    assert np.all(np.isnan(got[:, :3]))
+    assert np.all(got[:, 3] == 0.0)
+    assert np.all(got[:, 4] == got[:, 5])
+    _check(x[4:], got[:, 4:], 32, "special")
+
+
+def test_bitwise_deterministic():
+    x = W.mixture_c2(100000, seed=3)
+    a = _eval(x, 32)
+    b = _eval(x, 32)
+    assert np.array_equal(a, b)
+
+
+def test_kmax_prefix_consistency():
+    """Lower-kmax results agree with the oracle at the same tolerance; the
+    anchor order changes with kmax in region A, so values differ in the last
+    bits but never beyond eps_tol."""
+    x = W.mixture_c1(20000, seed=5)
+    full = _eval(x, 32)
+    for kmax in (0, 4, 16):
+        part = _eval(x, kmax)
+        assert np.max(np.abs(part - full[:kmax + 1])) <= 2 * EPS
+
+
+def test_c2_full_size_sampled():
+    """The headline workload at its full size (N = 2^26, kmax = 32, the launch
+    bench.py times), checked on 2^15 sampled arguments plus every argument
+    within 1e-9 of a region boundary and every zero."""
+    n = 1 << 26
+    x = W.mixture_c2(n, seed=1)
+    xt = torch.from_numpy(x).to(DEV)
+    out = pb.boys_eval(xt, 32)
+    rng = np.random.default_rng(1234)
+    idx = rng.choice(n, size=1 << 15, replace=False)
+    special = np.nonzero((np.abs(x - W.X0_PRINTED) < 1e-9) | (np.abs(x - W.X1_PRINTED) < 1e-9) | (x == 0))[0]
+    idx = np.unique(np.concatenate([idx, special]))
+    got = out[:, torch.from_numpy(idx).to(DEV)].cpu().numpy()
+    _check(x[idx], got, 32, "c2 sample")
+    del out, xt
+    torch.cuda.empty_cache()
+
+
+def _fused_tol(x, rho, kmax):
+    hi, _ = oracle.boys(x, kmax)
+    a = (2.0 * rho)[None, :] ** np.arange(kmax + 1)[:, None]
+    return EPS * a.sum(axis=0) + 64 * 2.0 ** -53 * np.abs(a * hi).sum(axis=0) + SLACK
+
+
+@pytest.mark.parametrize("kmax", [0, 1, 4, 8, 16, 24, 32])
+def test_fused_against_oracle(kmax):
+    x = np.concatenate([W.mixture_c2(20000, seed=40 + kmax), W.small_parity_set()[:-1]])
+    x = x[np.isfinite(x) & (x >= 0) & (x < 1e300)]
+    rho = W.rho_c2(x.size, seed=2)
+    out = pb.boys_eval_fused(torch.from_numpy(x).to(DEV), torch.from_numpy(rho).to(DEV), kmax)
+    torch.cuda.synchronize()
+    got = out.cpu().numpy()
+    hi, lo = oracle.fused(x, rho, kmax)
+    err = _err(got, hi, lo)
+    tol = _fused_tol(x, rho, kmax)
+    assert np.all(err <= tol), f"kmax={kmax}: worst ratio {np.max(err / tol):.3f}"
+
+
+def test_fused_c2_full_size_sampled():
+    n = 1 << 26
+    x = W.mixture_c2(n, seed=1)
+    rho = W.rho_c2(n, seed=2)
+    out = pb.boys_eval_fused(torch.from_numpy(x).to(DEV), torch.from_numpy(rho).to(DEV), 32)
+    idx = np.random.default_rng(99).choice(n, size=1 << 14, replace=False)
+    got = out[torch.from_numpy(idx).to(DEV)].cpu().numpy()
+    hi, lo = oracle.fused(x[idx], rho[idx], 32)
+    err = _err(got, hi, lo)
+    tol = _fused_tol(x[idx], rho[idx], 32)
+    assert np.all(err <= tol), f"worst ratio {np.max(err / tol):.3f}"
+
+
+def test_argument_errors_on_device():
+    xt = torch.zeros(8, dtype=torch.float64, device=DEV)
+    with pytest.raises(pb._lib.BoysError):
+        pb.boys_eval(xt, 33)
+    with pytest.raises(TypeError):
+        pb.boys_eval(xt.float(), 4)
