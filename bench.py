@@ -48,9 +48,10 @@ WORKLOAD = "boys_fp64_stored_kmax32_n2^26_eri_mixture"
 # 1.19 TFLOP/s, 95% of it).  Burst HBM copy bandwidth is driver-measured.
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 HBM_FALLBACK_GBS = 6800.0
-# DRAM bytes per argument of the timed kernel from an ncu capture (profiles/);
-# None until a capture of the current kernel exists.
-TRAFFIC_BYTES_PER_X = None
+# DRAM bytes per argument of the timed kernel from one ncu capture at N = 2^22
+# (profiles/k_eval_f64_kmax32_eri_mixture.md), scaled to the launch by the
+# arguments it processes; None whenever the kernel changed since that capture.
+TRAFFIC_BYTES_PER_X = 257.7
 
 
 def peaks():
