@@ -33,6 +33,7 @@
 #ifndef LIBBOYS_BOYS_H
 #define LIBBOYS_BOYS_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus
@@ -82,6 +83,73 @@ boys_status boys_eval(const double* x, int64_t n, int kmax, double* out, int64_t
  */
 boys_status boys_eval_fused(const double* x, const double* rho, int64_t n, int kmax,
                             double* out, void* stream);
+
+/*
+ * Backward pass: dF_k/dx = -F_{k+1} (Eq. 3 differentiated under the integral
+ * sign), so for upstream gradients g_k = dL/dF_k
+ *   dx[i] = -sum_{k=0}^{kmax} g[k*ldg + i] * F_{k+1}(x_i).
+ * F_0..F_{kmax+1} are re-evaluated in-kernel at order kmax+1, hence
+ * 0 <= kmax <= 31.  x [n], g [kmax+1][ldg] (ldg >= n), dx [n] (overwritten).
+ */
+boys_status boys_grad(const double* x, int64_t n, int kmax, const double* g, int64_t ldg,
+                      double* dx, void* stream);
+
+/*
+ * Ragged batches — many segments with their own kmax in ONE persistent
+ * launch (e.g. the shell quartets of an ERI batch, kmax_s = la+lb+lc+ld).
+ *   x        [total]    all arguments, segment s owning x[seg_off[s] .. seg_off[s+1])
+ *   seg_off  [nseg+1]   int64, seg_off[0] = 0, non-decreasing (empty segments allowed)
+ *   seg_kmax [nseg]     int32 in [0, 32]
+ *   out_off  [nseg]     int64 element offset of segment s's output block
+ *   out                 F_k(x[seg_off[s] + j]) at out[out_off[s] + k*len_s + j],
+ *                       len_s = seg_off[s+1] - seg_off[s]  (an order-major block)
+ *   workspace           device scratch of boys_ragged_workspace_size() bytes,
+ *                       16-byte aligned, owned by the caller; it holds the
+ *                       persistent kernel's work counter (reset by a memset
+ *                       enqueued before each launch) and an error word.  Calls
+ *                       that share a workspace must not overlap on the GPU.
+ * Every argument is evaluated by the same code as boys_eval at its segment's
+ * kmax, so results are bitwise identical to per-segment boys_eval calls.
+ * Descriptors live on the device and are not validated on the host; a
+ * segment whose kmax is outside [0, 32] is skipped and flags the workspace
+ * (see boys_ragged_status).
+ */
+size_t boys_ragged_workspace_size(void);
+boys_status boys_eval_ragged(const double* x, const int64_t* seg_off, const int32_t* seg_kmax,
+                             int32_t nseg, double* out, const int64_t* out_off, void* workspace,
+                             size_t workspace_bytes, void* stream);
+
+/* Reads the error word of a ragged workspace after the stream's work so far
+ * (synchronises `stream`): *bad_kmax = 1 if a segment had kmax outside [0, 32]. */
+boys_status boys_ragged_status(const void* workspace, int* bad_kmax, void* stream);
+
+/*
+ * Ragged plan: fixes the buffers and descriptors of a ragged batch, picks the
+ * launch shape (block size 64/128/256, 1 or 2 arguments per thread, 1 or 2
+ * resident waves) and captures workspace reset + persistent kernel into a
+ * CUDA graph; boys_ragged_plan_launch then replays it with one
+ * cudaGraphLaunch.  Creation reads the descriptors back (it synchronises the
+ * device), validates them (seg_off[0] = 0, non-decreasing, kmax in [0, 32])
+ * and allocates a 256-byte workspace that the plan owns.
+ *   flags & BOYS_PLAN_AUTOTUNE      time every candidate shape on these very
+ *                                   buffers (outputs are overwritten) and
+ *                                   keep the fastest; results are cached per
+ *                                   device/driver/library/workload key in
+ *                                   memory and, if the environment variable
+ *                                   BOYS_AUTOTUNE_CACHE names a file, on disk.
+ *   flags & BOYS_PLAN_FORCE_CONFIG  take the shape from BOYS_FORCE_CONFIG =
+ *                                   "block,xpt,waves" (for tests).
+ * Without flags the default shape (128, 1, 1) is used.
+ */
+#define BOYS_PLAN_AUTOTUNE 1
+#define BOYS_PLAN_FORCE_CONFIG 2
+typedef struct boys_ragged_plan boys_ragged_plan;
+boys_status boys_ragged_plan_create(const double* x, const int64_t* seg_off, const int32_t* seg_kmax,
+                                    int32_t nseg, double* out, const int64_t* out_off, int flags,
+                                    boys_ragged_plan** plan);
+boys_status boys_ragged_plan_launch(boys_ragged_plan* plan, void* stream);
+boys_status boys_ragged_plan_config(const boys_ragged_plan* plan, int* block, int* xpt, int* waves);
+void boys_ragged_plan_destroy(boys_ragged_plan* plan);
 
 #ifdef __cplusplus
 }

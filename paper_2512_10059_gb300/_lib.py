@@ -30,6 +30,14 @@ def _declare(lib):
         "boys_kmax_limit": (i32, []),
         "boys_eval": (i32, [vp, i64, i32, vp, i64, vp]),
         "boys_eval_fused": (i32, [vp, vp, i64, i32, vp, vp]),
+        "boys_grad": (i32, [vp, i64, i32, vp, i64, vp, vp]),
+        "boys_ragged_workspace_size": (ctypes.c_size_t, []),
+        "boys_eval_ragged": (i32, [vp, vp, vp, i32, vp, vp, vp, ctypes.c_size_t, vp]),
+        "boys_ragged_status": (i32, [vp, ctypes.POINTER(i32), vp]),
+        "boys_ragged_plan_create": (i32, [vp, vp, vp, i32, vp, vp, i32, ctypes.POINTER(vp)]),
+        "boys_ragged_plan_launch": (i32, [vp, vp]),
+        "boys_ragged_plan_config": (i32, [vp, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32)]),
+        "boys_ragged_plan_destroy": (None, [vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)

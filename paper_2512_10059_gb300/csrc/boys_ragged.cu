@@ -1,0 +1,422 @@
+// Ragged batches: many segments, each with its own kmax (e.g. the shell
+// quartets of an ERI batch, kmax_s = la+lb+lc+ld), in ONE persistent launch.
+//
+// Work decomposition: the concatenated argument array x[0, total) is cut into
+// flat tiles of blockDim*XPT arguments; resident CTAs take tiles from a
+// global atomic counter (the only scratch memory) until none are left, which
+// balances the very uneven per-argument cost of different kmax.  A thread
+// finds the segment of each of its arguments by binary search over seg_off
+// restricted to the tile's segment range, and evaluates it with exactly the
+// code boys_eval uses for that segment's kmax (bitwise-identical results).
+// A warp whose lanes straddle segments with different kmax loops over the
+// distinct values (rare: only warps that cross a segment boundary).
+//
+// Output of segment s (length len_s = seg_off[s+1] - seg_off[s]) is its own
+// order-major block: F_k(x[seg_off[s] + j]) at out[out_off[s] + k*len_s + j].
+#include <algorithm>
+#include <array>
+#include <chrono>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <unordered_map>
+#include <utility>
+#include <vector>
+
+#include "boys_fp64.cuh"
+#include "boys_internal.h"
+
+namespace boys {
+namespace ragged {
+
+constexpr int kMaxBlock = 256;
+
+struct Workspace {
+    unsigned long long next_tile;  // work counter, zeroed before every launch
+    unsigned long long error;      // nonzero: a segment had kmax outside [0, 32]
+};
+static_assert(sizeof(Workspace) <= 256, "workspace fits its published size");
+
+template <int K>
+__device__ __noinline__ void eval_store(double xv, double* __restrict__ dst, int64_t row) {
+    double F[K + 1];
+    fp64::eval_point<K>(xv, F);
+#pragma unroll
+    for (int k = 0; k <= K; ++k) __stcs(dst + k * row, F[k]);
+}
+
+__device__ __forceinline__ void dispatch(int k, double xv, double* dst, int64_t row) {
+#define BOYS_RAGGED_CASE(K) \
+    case K: eval_store<K>(xv, dst, row); break;
+    switch (k) {
+        BOYS_RAGGED_CASE(0) BOYS_RAGGED_CASE(1) BOYS_RAGGED_CASE(2) BOYS_RAGGED_CASE(3)
+        BOYS_RAGGED_CASE(4) BOYS_RAGGED_CASE(5) BOYS_RAGGED_CASE(6) BOYS_RAGGED_CASE(7)
+        BOYS_RAGGED_CASE(8) BOYS_RAGGED_CASE(9) BOYS_RAGGED_CASE(10) BOYS_RAGGED_CASE(11)
+        BOYS_RAGGED_CASE(12) BOYS_RAGGED_CASE(13) BOYS_RAGGED_CASE(14) BOYS_RAGGED_CASE(15)
+        BOYS_RAGGED_CASE(16) BOYS_RAGGED_CASE(17) BOYS_RAGGED_CASE(18) BOYS_RAGGED_CASE(19)
+        BOYS_RAGGED_CASE(20) BOYS_RAGGED_CASE(21) BOYS_RAGGED_CASE(22) BOYS_RAGGED_CASE(23)
+        BOYS_RAGGED_CASE(24) BOYS_RAGGED_CASE(25) BOYS_RAGGED_CASE(26) BOYS_RAGGED_CASE(27)
+        BOYS_RAGGED_CASE(28) BOYS_RAGGED_CASE(29) BOYS_RAGGED_CASE(30) BOYS_RAGGED_CASE(31)
+        BOYS_RAGGED_CASE(32)
+        default: break;
+    }
+#undef BOYS_RAGGED_CASE
+}
+
+// Largest s in [lo, hi] with seg_off[s] <= i (seg_off non-decreasing).
+__device__ __forceinline__ int find_segment(const int64_t* __restrict__ seg_off, int lo, int hi, int64_t i) {
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(seg_off + mid) <= i) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+template <int XPT>
+__global__ void __launch_bounds__(kMaxBlock) k_ragged(const double* __restrict__ x,
+                                                      const int64_t* __restrict__ seg_off,
+                                                      const int32_t* __restrict__ seg_kmax, int nseg,
+                                                      double* __restrict__ out,
+                                                      const int64_t* __restrict__ out_off,
+                                                      Workspace* __restrict__ ws) {
+    __shared__ long long s_tile;
+    __shared__ int s_seg_lo, s_seg_hi;
+    const int64_t total = __ldg(seg_off + nseg);
+    const int64_t per_tile = (int64_t)blockDim.x * XPT;
+    const int64_t ntiles = (total + per_tile - 1) / per_tile;
+    const unsigned lane = threadIdx.x & 31;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            const long long t = (long long)atomicAdd(&ws->next_tile, 1ULL);
+            s_tile = t;
+            if (t < ntiles) {
+                const int64_t first = t * per_tile;
+                const int64_t last = min(first + per_tile, total) - 1;
+                const int lo = find_segment(seg_off, 0, nseg - 1, first);
+                s_seg_lo = lo;
+                s_seg_hi = find_segment(seg_off, lo, nseg - 1, last);
+            }
+        }
+        __syncthreads();
+        const long long t = s_tile;
+        const int seg_lo = s_seg_lo, seg_hi = s_seg_hi;
+        __syncthreads();
+        if (t >= ntiles) break;
+        const int64_t base = t * per_tile;
+#pragma unroll 1
+        for (int j = 0; j < XPT; ++j) {
+            const int64_t i = base + (int64_t)j * blockDim.x + threadIdx.x;
+            bool valid = i < total;
+            int km = 0;
+            double xv = 0.0;
+            double* dst = nullptr;
+            int64_t row = 0;
+            if (valid) {
+                const int s = find_segment(seg_off, seg_lo, seg_hi, i);
+                const int64_t s0 = __ldg(seg_off + s);
+                row = __ldg(seg_off + s + 1) - s0;
+                km = __ldg(seg_kmax + s);
+                if (km < 0 || km > 32) {
+                    atomicOr(&ws->error, 1ULL);
+                    valid = false;
+                } else {
+                    xv = __ldcs(x + i);
+                    dst = out + __ldg(out_off + s) + (i - s0);
+                }
+            }
+            unsigned pending = __ballot_sync(0xffffffffu, valid);
+            while (pending) {
+                const int leader = __ffs(pending) - 1;
+                const int k = __shfl_sync(0xffffffffu, km, leader);
+                const bool mine = valid && km == k && ((pending >> lane) & 1u);
+                if (mine) dispatch(k, xv, dst, row);
+                pending &= ~__ballot_sync(0xffffffffu, mine);
+            }
+        }
+    }
+}
+
+using KernelFn = void (*)(const double*, const int64_t*, const int32_t*, int, double*, const int64_t*, Workspace*);
+
+inline KernelFn kernel_for(int xpt) { return xpt == 2 ? &k_ragged<2> : &k_ragged<1>; }
+
+struct Config {
+    int block = 128;
+    int xpt = 1;
+    int waves = 1;  // resident CTAs per SM multiplier for the persistent grid
+};
+
+inline int grid_size(const Config& c) {
+    const int per_sm = blocks_per_sm((const void*)kernel_for(c.xpt), c.block);
+    return std::max(1, sm_count() * per_sm * c.waves);
+}
+
+boys_status check_args(const double* x, const int64_t* seg_off, const int32_t* seg_kmax, int32_t nseg,
+                       double* out, const int64_t* out_off, const char* fn) {
+    if (nseg < 0) return fail(BOYS_ERR_INVALID_ARG, "%s: nseg=%d < 0", fn, nseg);
+    if (nseg == 0) return BOYS_OK;
+    if (!x || !seg_off || !seg_kmax || !out || !out_off) return fail(BOYS_ERR_INVALID_ARG, "%s: NULL pointer", fn);
+    if (!aligned(x, 8) || !aligned(out, 8) || !aligned(seg_off, 8) || !aligned(out_off, 8) || !aligned(seg_kmax, 4))
+        return fail(BOYS_ERR_ALIGNMENT, "%s: pointer not aligned to its element size", fn);
+    return BOYS_OK;
+}
+
+boys_status launch(const Config& c, const double* x, const int64_t* seg_off, const int32_t* seg_kmax, int32_t nseg,
+                   double* out, const int64_t* out_off, Workspace* ws, cudaStream_t stream) {
+    boys_status st = check_cuda(cudaMemsetAsync(ws, 0, sizeof(Workspace), stream), "ragged workspace reset");
+    if (st != BOYS_OK) return st;
+    kernel_for(c.xpt)<<<grid_size(c), c.block, 0, stream>>>(x, seg_off, seg_kmax, nseg, out, out_off, ws);
+    return check_cuda(cudaGetLastError(), "ragged launch");
+}
+
+// ------------------------------------------------------------- autotuning
+
+const std::vector<Config>& candidates() {
+    static const std::vector<Config> c = [] {
+        std::vector<Config> v;
+        for (int block : {64, 128, 256})
+            for (int xpt : {1, 2})
+                for (int waves : {1, 2}) v.push_back(Config{block, xpt, waves});
+        return v;
+    }();
+    return c;
+}
+
+std::string device_key() {
+    int dev = 0, drv = 0;
+    cudaGetDevice(&dev);
+    cudaDriverGetVersion(&drv);
+    cudaDeviceProp p;
+    if (cudaGetDeviceProperties(&p, dev) != cudaSuccess) return "unknown";
+    char buf[512];
+    snprintf(buf, sizeof(buf), "%.200s|sm%d%d|%dSM|drv%d|lib%d", p.name, p.major, p.minor, p.multiProcessorCount, drv,
+             boys_version());
+    for (char* q = buf; *q; ++q)
+        if (*q == ' ') *q = '_';
+    return buf;
+}
+
+struct TuneCache {
+    std::mutex mu;
+    std::unordered_map<std::string, Config> mem;
+    bool loaded = false;
+
+    static const char* path() { return getenv("BOYS_AUTOTUNE_CACHE"); }
+
+    void load() {
+        if (loaded) return;
+        loaded = true;
+        const char* p = path();
+        if (!p) return;
+        FILE* f = fopen(p, "r");
+        if (!f) return;
+        char key[512];
+        Config c;
+        while (fscanf(f, "%511s %d %d %d", key, &c.block, &c.xpt, &c.waves) == 4) mem[key] = c;
+        fclose(f);
+    }
+
+    bool get(const std::string& k, Config* c) {
+        std::lock_guard<std::mutex> lk(mu);
+        load();
+        auto it = mem.find(k);
+        if (it == mem.end()) return false;
+        *c = it->second;
+        return true;
+    }
+
+    void put(const std::string& k, const Config& c) {
+        std::lock_guard<std::mutex> lk(mu);
+        load();
+        mem[k] = c;
+        const char* p = path();
+        if (!p) return;
+        FILE* f = fopen(p, "a");
+        if (!f) return;
+        fprintf(f, "%s %d %d %d\n", k.c_str(), c.block, c.xpt, c.waves);
+        fclose(f);
+    }
+};
+
+TuneCache& cache() {
+    static TuneCache c;
+    return c;
+}
+
+}  // namespace ragged
+}  // namespace boys
+
+using namespace boys;
+
+struct boys_ragged_plan {
+    const double* x;
+    const int64_t* seg_off;
+    const int32_t* seg_kmax;
+    int32_t nseg;
+    double* out;
+    const int64_t* out_off;
+    ragged::Workspace* ws;
+    ragged::Config cfg;
+    int64_t total;
+    cudaGraph_t graph;
+    cudaGraphExec_t exec;
+    float tuned_ms;
+};
+
+BOYS_API size_t boys_ragged_workspace_size(void) { return 256; }
+
+BOYS_API boys_status boys_eval_ragged(const double* x, const int64_t* seg_off, const int32_t* seg_kmax,
+                                      int32_t nseg, double* out, const int64_t* out_off, void* workspace,
+                                      size_t workspace_bytes, void* stream) {
+    boys_status st = ragged::check_args(x, seg_off, seg_kmax, nseg, out, out_off, "boys_eval_ragged");
+    if (st != BOYS_OK || nseg == 0) return st;
+    if (!workspace) return fail(BOYS_ERR_INVALID_ARG, "boys_eval_ragged: NULL workspace");
+    if (workspace_bytes < boys_ragged_workspace_size())
+        return fail(BOYS_ERR_INVALID_ARG, "boys_eval_ragged: workspace_bytes=%zu < %zu", workspace_bytes,
+                    boys_ragged_workspace_size());
+    if (!aligned(workspace, 16)) return fail(BOYS_ERR_ALIGNMENT, "boys_eval_ragged: workspace not 16-byte aligned");
+    ragged::Config c;
+    return ragged::launch(c, x, seg_off, seg_kmax, nseg, out, out_off, (ragged::Workspace*)workspace,
+                          (cudaStream_t)stream);
+}
+
+BOYS_API boys_status boys_ragged_status(const void* workspace, int* bad_kmax, void* stream) {
+    if (!workspace || !bad_kmax) return fail(BOYS_ERR_INVALID_ARG, "boys_ragged_status: NULL pointer");
+    unsigned long long err = 0;
+    const ragged::Workspace* ws = (const ragged::Workspace*)workspace;
+    boys_status st = check_cuda(cudaMemcpyAsync(&err, &ws->error, sizeof(err), cudaMemcpyDeviceToHost,
+                                                (cudaStream_t)stream), "boys_ragged_status copy");
+    if (st != BOYS_OK) return st;
+    st = check_cuda(cudaStreamSynchronize((cudaStream_t)stream), "boys_ragged_status sync");
+    *bad_kmax = err ? 1 : 0;
+    return st;
+}
+
+static boys_status capture_graph(boys_ragged_plan* p) {
+    cudaStream_t s;
+    boys_status st = check_cuda(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking), "plan stream");
+    if (st != BOYS_OK) return st;
+    st = check_cuda(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal), "begin capture");
+    if (st == BOYS_OK) {
+        boys_status lst = ragged::launch(p->cfg, p->x, p->seg_off, p->seg_kmax, p->nseg, p->out, p->out_off, p->ws, s);
+        cudaGraph_t g = nullptr;
+        boys_status est = check_cuda(cudaStreamEndCapture(s, &g), "end capture");
+        st = lst != BOYS_OK ? lst : est;
+        if (st == BOYS_OK) {
+            p->graph = g;
+            st = check_cuda(cudaGraphInstantiate(&p->exec, g, 0), "graph instantiate");
+        } else if (g) {
+            cudaGraphDestroy(g);
+        }
+    }
+    cudaStreamDestroy(s);
+    return st;
+}
+
+static float time_config(boys_ragged_plan* p, const ragged::Config& c, cudaStream_t s, int reps) {
+    cudaEvent_t a, b;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    ragged::launch(c, p->x, p->seg_off, p->seg_kmax, p->nseg, p->out, p->out_off, p->ws, s);  // warm
+    cudaEventRecord(a, s);
+    for (int r = 0; r < reps; ++r)
+        ragged::launch(c, p->x, p->seg_off, p->seg_kmax, p->nseg, p->out, p->out_off, p->ws, s);
+    cudaEventRecord(b, s);
+    float ms = -1.0f;
+    if (cudaEventSynchronize(b) == cudaSuccess) cudaEventElapsedTime(&ms, a, b);
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    return ms / reps;
+}
+
+BOYS_API boys_status boys_ragged_plan_create(const double* x, const int64_t* seg_off, const int32_t* seg_kmax,
+                                             int32_t nseg, double* out, const int64_t* out_off, int flags,
+                                             boys_ragged_plan** plan) {
+    if (!plan) return fail(BOYS_ERR_INVALID_ARG, "boys_ragged_plan_create: NULL plan");
+    *plan = nullptr;
+    boys_status st = ragged::check_args(x, seg_off, seg_kmax, nseg, out, out_off, "boys_ragged_plan_create");
+    if (st != BOYS_OK) return st;
+    if (nseg == 0) return fail(BOYS_ERR_INVALID_ARG, "boys_ragged_plan_create: nseg must be > 0");
+    // Read the descriptors once (plan creation is a set-up step and may synchronise).
+    std::vector<int64_t> off(nseg + 1);
+    std::vector<int32_t> km(nseg);
+    st = check_cuda(cudaMemcpy(off.data(), seg_off, sizeof(int64_t) * (nseg + 1), cudaMemcpyDeviceToHost), "read seg_off");
+    if (st != BOYS_OK) return st;
+    st = check_cuda(cudaMemcpy(km.data(), seg_kmax, sizeof(int32_t) * nseg, cudaMemcpyDeviceToHost), "read seg_kmax");
+    if (st != BOYS_OK) return st;
+    int64_t hist[33] = {0};
+    for (int32_t s = 0; s < nseg; ++s) {
+        if (off[s + 1] < off[s]) return fail(BOYS_ERR_INVALID_ARG, "boys_ragged_plan_create: seg_off decreases at %d", s);
+        if (km[s] < 0 || km[s] > 32) return fail(BOYS_ERR_KMAX, "boys_ragged_plan_create: seg_kmax[%d]=%d", s, km[s]);
+        hist[km[s]] += off[s + 1] - off[s];
+    }
+    if (off[0] != 0) return fail(BOYS_ERR_INVALID_ARG, "boys_ragged_plan_create: seg_off[0] must be 0");
+
+    boys_ragged_plan* p = new boys_ragged_plan{};
+    p->x = x; p->seg_off = seg_off; p->seg_kmax = seg_kmax; p->nseg = nseg; p->out = out; p->out_off = out_off;
+    p->total = off[nseg];
+    st = check_cuda(cudaMalloc((void**)&p->ws, 256), "plan workspace");
+    if (st != BOYS_OK) { delete p; return st; }
+
+    if (flags & BOYS_PLAN_AUTOTUNE) {
+        // workload key: device + size bucket + argument-weighted kmax histogram (coarse)
+        char wk[256];
+        int64_t wsum = 0;
+        for (int k = 0; k <= 32; ++k) wsum += hist[k] * (k + 1);
+        snprintf(wk, sizeof(wk), "|n2^%d|seg%d|w%.2f", 64 - __builtin_clzll((unsigned long long)std::max<int64_t>(1, p->total)),
+                 nseg, p->total ? (double)wsum / p->total : 0.0);
+        const std::string key = ragged::device_key() + wk;
+        ragged::Config best;
+        if (!ragged::cache().get(key, &best)) {
+            cudaStream_t s;
+            cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+            float best_ms = 1e30f;
+            for (const auto& c : ragged::candidates()) {
+                const float ms = time_config(p, c, s, 3);
+                if (ms > 0 && ms < best_ms) { best_ms = ms; best = c; }
+            }
+            cudaStreamSynchronize(s);
+            cudaStreamDestroy(s);
+            p->tuned_ms = best_ms;
+            st = check_cuda(cudaGetLastError(), "autotune");
+            if (st != BOYS_OK) { cudaFree(p->ws); delete p; return st; }
+            ragged::cache().put(key, best);
+        }
+        p->cfg = best;
+    }
+    if (flags & BOYS_PLAN_FORCE_CONFIG) {
+        // BOYS_FORCE_CONFIG="block,xpt,waves" overrides tuning (tests use it)
+        const char* f = getenv("BOYS_FORCE_CONFIG");
+        ragged::Config c;
+        if (f && sscanf(f, "%d,%d,%d", &c.block, &c.xpt, &c.waves) == 3 && (c.block == 64 || c.block == 128 || c.block == 256) &&
+            (c.xpt == 1 || c.xpt == 2) && c.waves >= 1 && c.waves <= 8)
+            p->cfg = c;
+    }
+    st = capture_graph(p);
+    if (st != BOYS_OK) { cudaFree(p->ws); delete p; return st; }
+    *plan = p;
+    return BOYS_OK;
+}
+
+BOYS_API boys_status boys_ragged_plan_launch(boys_ragged_plan* plan, void* stream) {
+    if (!plan) return fail(BOYS_ERR_INVALID_ARG, "boys_ragged_plan_launch: NULL plan");
+    return check_cuda(cudaGraphLaunch(plan->exec, (cudaStream_t)stream), "graph launch");
+}
+
+BOYS_API boys_status boys_ragged_plan_config(const boys_ragged_plan* plan, int* block, int* xpt, int* waves) {
+    if (!plan || !block || !xpt || !waves) return fail(BOYS_ERR_INVALID_ARG, "boys_ragged_plan_config: NULL pointer");
+    *block = plan->cfg.block;
+    *xpt = plan->cfg.xpt;
+    *waves = plan->cfg.waves;
+    return BOYS_OK;
+}
+
+BOYS_API void boys_ragged_plan_destroy(boys_ragged_plan* plan) {
+    if (!plan) return;
+    if (plan->exec) cudaGraphExecDestroy(plan->exec);
+    if (plan->graph) cudaGraphDestroy(plan->graph);
+    if (plan->ws) cudaFree(plan->ws);
+    delete plan;
+}

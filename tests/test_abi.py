@@ -58,3 +58,27 @@ def test_fused_argument_errors(L):
     assert L.boys_eval_fused(FAKE, None, 10, 3, FAKE, None) == 1
     assert L.boys_eval_fused(FAKE, FAKE + 2, 10, 3, FAKE, None) == 3
     assert L.boys_eval_fused(None, None, 0, 3, None, None) == 0
+
+
+def test_grad_argument_errors(L):
+    assert L.boys_grad(FAKE, 10, 32, FAKE, 10, FAKE, None) == 2  # needs F_{kmax+1} <= F_32
+    assert L.boys_grad(FAKE, 10, 4, FAKE, 9, FAKE, None) == 1
+    assert L.boys_grad(FAKE, 10, 4, None, 10, FAKE, None) == 1
+    assert L.boys_grad(None, 0, 4, None, 0, None, None) == 0
+
+
+def test_ragged_argument_errors(L):
+    import ctypes
+    assert L.boys_ragged_workspace_size() == 256
+    assert L.boys_eval_ragged(FAKE, FAKE, FAKE, -1, FAKE, FAKE, FAKE, 256, None) == 1
+    assert L.boys_eval_ragged(None, None, None, 0, None, None, None, 0, None) == 0
+    assert L.boys_eval_ragged(FAKE, None, FAKE, 3, FAKE, FAKE, FAKE, 256, None) == 1
+    assert L.boys_eval_ragged(FAKE, FAKE, FAKE, 3, FAKE, FAKE, FAKE, 255, None) == 1
+    assert L.boys_eval_ragged(FAKE, FAKE, FAKE, 3, FAKE, FAKE, None, 256, None) == 1
+    assert L.boys_eval_ragged(FAKE, FAKE, FAKE + 2, 3, FAKE, FAKE, FAKE, 256, None) == 3
+    assert L.boys_eval_ragged(FAKE, FAKE, FAKE, 3, FAKE, FAKE, FAKE + 8, 256, None) == 3
+    h = ctypes.c_void_p()
+    assert L.boys_ragged_plan_create(FAKE, FAKE, FAKE, 0, FAKE, FAKE, 0, ctypes.byref(h)) == 1
+    assert L.boys_ragged_plan_create(FAKE, FAKE, FAKE, 3, FAKE, FAKE, 0, None) == 1
+    assert L.boys_ragged_plan_launch(None, None) == 1
+    L.boys_ragged_plan_destroy(None)
