@@ -1,6 +1,6 @@
 """Generate ``boys_coeffs_fp64.h`` from the coefficient tables of the paper.
 
-Usage:  python gen_coeffs_fp64.py /root/reference/PAPER.md > boys_coeffs_fp64.h
+Usage:  python gen_coeffs_fp64.py <the paper's LaTeX source> > boys_coeffs_fp64.h
 
 The paper's Appendix D prints, for eps_tol = 5e-14 and kmax = 32:
   * the region boundaries x_0 and x_1 (Eqs. value_of_x0 / value_of_x1),
