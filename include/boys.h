@@ -151,6 +151,28 @@ boys_status boys_ragged_plan_launch(boys_ragged_plan* plan, void* stream);
 boys_status boys_ragged_plan_config(const boys_ragged_plan* plan, int* block, int* xpt, int* waves);
 void boys_ragged_plan_destroy(boys_ragged_plan* plan);
 
+/*
+ * Ragged batch that allocates nothing.  The paper has no counterpart; this is
+ * for callers that cannot provide device memory of their own, e.g. code that
+ * must not call cudaMalloc because a framework or an application's fixed
+ * memory budget owns every device allocation, or a latency-critical loop that
+ * cannot take cudaMalloc's implicit synchronisation.  Same arguments, layout
+ * and results as boys_eval_ragged, without the workspace: the persistent
+ * kernel's scratch (a 16-byte tile counter and error word) lives in a 256-byte
+ * array inside the library's device image, held by every GPU that loads the
+ * library until the process exits.  The scratch need does not grow with nseg
+ * or the argument count, so no call exceeds the array (the check is kept).
+ *  * The first call on each device, with that device current, looks up the
+ *    array's device address (cudaGetSymbolAddress, which may load the
+ *    library's device code); make that first call before any stream capture.
+ *  * Every call on a device shares the one array and re-zeroes its counter on
+ *    `stream` first: calls that overlap on the GPU (other streams, other host
+ *    threads) race with each other and produce wrong output.
+ *  * No cudaMalloc, cudaFree or other allocating routine is called.
+ */
+boys_status boys_eval_ragged_noalloc(const double* x, const int64_t* seg_off, const int32_t* seg_kmax,
+                                     int32_t nseg, double* out, const int64_t* out_off, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -21,6 +21,9 @@ class BoysError(RuntimeError):
         self.status = status
 
 
+SIGNATURES = {}
+
+
 def _declare(lib):
     i64, i32, vp = ctypes.c_int64, ctypes.c_int, ctypes.c_void_p
     sig = {
@@ -38,7 +41,9 @@ def _declare(lib):
         "boys_ragged_plan_launch": (i32, [vp, vp]),
         "boys_ragged_plan_config": (i32, [vp, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32)]),
         "boys_ragged_plan_destroy": (None, [vp]),
+        "boys_eval_ragged_noalloc": (i32, [vp, vp, vp, i32, vp, vp, vp]),
     }
+    SIGNATURES.update(sig)
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
         fn.restype = res

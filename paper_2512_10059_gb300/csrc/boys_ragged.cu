@@ -420,3 +420,75 @@ BOYS_API void boys_ragged_plan_destroy(boys_ragged_plan* plan) {
     if (plan->ws) cudaFree(plan->ws);
     delete plan;
 }
+
+// ------------------------------------------------ ragged batch without allocation
+//
+// boys_eval_ragged_noalloc serves callers that cannot hand the library any
+// device memory of their own: the ragged kernel's scratch (tile counter and
+// error word, 16 bytes) lives instead in the array below, which is part of
+// this library's device image.  Every GPU that loads the library holds the
+// array (kNoAllocScratchBytes) until the process exits.
+
+namespace boys {
+namespace ragged {
+
+constexpr size_t kNoAllocScratchBytes = 256;
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+static_assert(sizeof(Workspace) <= kNoAllocScratchBytes, "ragged scratch must fit the static array");
+
+constexpr int kNoAllocMaxDevices = 64;
+static std::mutex g_noalloc_mu;
+static void* g_noalloc_ptr[kNoAllocMaxDevices];   // device address of the array, per device
+static int g_noalloc_grid[kNoAllocMaxDevices];    // persistent grid of k_ragged<1> at 128 threads
+
+// Per-device set-up on the first call with that device current: the array's
+// name is only a host-side stand-in, so its device address comes from
+// cudaGetSymbolAddress.  Nothing is allocated.
+static boys_status noalloc_setup(int dev, void** ptr, int* grid) {
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return check_cuda(e, "boys_eval_ragged_noalloc: cudaGetSymbolAddress");
+        int sms = 0, per_sm = 0;
+        e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return check_cuda(e, "boys_eval_ragged_noalloc: SM count");
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ragged<1>, 128, 0);
+        if (e != cudaSuccess) return check_cuda(e, "boys_eval_ragged_noalloc: occupancy");
+        g_noalloc_grid[dev] = std::max(1, sms * std::max(1, per_sm));
+        g_noalloc_ptr[dev] = p;
+    }
+    *ptr = g_noalloc_ptr[dev];
+    *grid = g_noalloc_grid[dev];
+    return BOYS_OK;
+}
+
+}  // namespace ragged
+}  // namespace boys
+
+BOYS_API boys_status boys_eval_ragged_noalloc(const double* x, const int64_t* seg_off, const int32_t* seg_kmax,
+                                              int32_t nseg, double* out, const int64_t* out_off, void* stream) {
+    boys_status st = ragged::check_args(x, seg_off, seg_kmax, nseg, out, out_off, "boys_eval_ragged_noalloc");
+    if (st != BOYS_OK || nseg == 0) return st;
+    // A call's scratch need does not grow with its sizes (one tile counter and
+    // one error word); it is checked against the array all the same.
+    if (sizeof(ragged::Workspace) > ragged::kNoAllocScratchBytes)
+        return fail(BOYS_ERR_INVALID_ARG, "boys_eval_ragged_noalloc: needs %zu bytes of scratch, the static array holds %zu",
+                    sizeof(ragged::Workspace), ragged::kNoAllocScratchBytes);
+    int dev = 0;
+    st = check_cuda(cudaGetDevice(&dev), "boys_eval_ragged_noalloc: cudaGetDevice");
+    if (st != BOYS_OK) return st;
+    if (dev < 0 || dev >= ragged::kNoAllocMaxDevices)
+        return fail(BOYS_ERR_INVALID_ARG, "boys_eval_ragged_noalloc: device %d beyond the %d supported", dev,
+                    ragged::kNoAllocMaxDevices);
+    void* scratch = nullptr;
+    int grid = 1;
+    st = ragged::noalloc_setup(dev, &scratch, &grid);
+    if (st != BOYS_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    // the array keeps the previous call's contents: the counter must restart at zero
+    st = check_cuda(cudaMemsetAsync(scratch, 0, sizeof(ragged::Workspace), s), "boys_eval_ragged_noalloc: scratch reset");
+    if (st != BOYS_OK) return st;
+    ragged::k_ragged<1><<<grid, 128, 0, s>>>(x, seg_off, seg_kmax, nseg, out, out_off, (ragged::Workspace*)scratch);
+    return check_cuda(cudaGetLastError(), "boys_eval_ragged_noalloc launch");
+}

@@ -82,3 +82,11 @@ def test_ragged_argument_errors(L):
     assert L.boys_ragged_plan_create(FAKE, FAKE, FAKE, 3, FAKE, FAKE, 0, None) == 1
     assert L.boys_ragged_plan_launch(None, None) == 1
     L.boys_ragged_plan_destroy(None)
+
+
+def test_every_declared_function_has_ctypes_signature(L):
+    """Without argtypes ctypes passes Python ints as 32-bit C ints, silently
+    truncating 64-bit device pointers: every entry point must be declared."""
+    for name in declared_functions():
+        assert name in _lib.SIGNATURES, f"{name} has no ctypes signature in _lib"
+        assert getattr(L, name).argtypes is not None or _lib.SIGNATURES[name][1] == []

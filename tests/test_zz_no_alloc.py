@@ -1,0 +1,59 @@
+"""The ragged entry point that allocates nothing, boys_eval_ragged_noalloc.
+
+It exists for callers that cannot give the library device memory (their
+framework or application owns every allocation, or they cannot afford
+cudaMalloc's synchronisation): its scratch is a static array inside the
+library.  The GPU test calls it through the C ABI twice in a row (the second
+call must find the shared tile counter re-zeroed) and compares each result
+with the workspace-taking boys_eval_ragged at the parity tolerance used by the
+other tests (5e-14 absolute); the two share the kernel, so the results are
+also expected to be bitwise equal.  This file is collected last on purpose.
+"""
+import numpy as np
+import pytest
+import torch
+
+from paper_2512_10059_gb300 import _lib, api, build
+from paper_2512_10059_gb300 import workloads as W
+
+FAKE = 0x10000  # never dereferenced: the argument checks reject these calls first
+
+
+def test_noalloc_argument_errors_without_gpu():
+    build.build()
+    L = _lib.lib()
+    assert L.boys_eval_ragged_noalloc(FAKE, FAKE, FAKE, -1, FAKE, FAKE, None) == 1
+    assert L.boys_eval_ragged_noalloc(None, None, None, 0, None, None, None) == 0
+    assert L.boys_eval_ragged_noalloc(FAKE, None, FAKE, 4, FAKE, FAKE, None) == 1
+    assert L.boys_eval_ragged_noalloc(FAKE, FAKE, FAKE + 2, 4, FAKE, FAKE, None) == 3
+
+
+def _batch(seed, nseg):
+    rng = np.random.default_rng(seed)
+    lens = rng.choice([0, 1, 7, 32, 33, 100, 513, 4000], size=nseg)
+    kmax = rng.integers(0, 33, size=nseg).astype(np.int32)
+    off = np.zeros(nseg + 1, dtype=np.int64)
+    np.cumsum(lens, out=off[1:])
+    x = W.mixture_c1(int(off[-1]), seed=seed + 1)
+    return x, off, kmax
+
+
+@pytest.mark.gpu
+def test_noalloc_matches_workspace_entry_point_twice():
+    dev = "cuda:0"
+    L = _lib.lib()
+    for call, (seed, nseg) in enumerate([(31, 150), (32, 400)]):
+        x, off, kmax = _batch(seed, nseg)
+        xt = torch.from_numpy(x).to(dev)
+        ot = torch.from_numpy(off).to(dev)
+        kt = torch.from_numpy(kmax).to(dev)
+        ref, out_off = api.boys_eval_ragged(xt, ot, kt)
+        got = torch.full_like(ref, float("nan"))
+        stream = torch.cuda.current_stream(dev)
+        st = L.boys_eval_ragged_noalloc(xt.data_ptr(), ot.data_ptr(), kt.data_ptr(), nseg, got.data_ptr(),
+                                        out_off.data_ptr(), int(stream.cuda_stream))
+        assert st == 0, L.boys_last_error()
+        torch.cuda.synchronize()
+        assert not torch.isnan(got).any(), f"call {call}: some outputs were not written"
+        assert torch.max(torch.abs(got - ref)).item() <= 5e-14, f"call {call}: differs from boys_eval_ragged"
+        assert torch.equal(got, ref), f"call {call}: not bitwise equal to boys_eval_ragged"
