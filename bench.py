@@ -302,6 +302,47 @@ def run_ours(args):
                  "hbm_gbs": n * 24 / (fms / 1e3) / 1e9}
         del rho, fout
 
+    # FP32 tier on the same arguments (rounded to float) and on the FP32-tier
+    # workload (parity mixture, N = 2^26) at kmax 4 / 12 / 24 next to FP64
+    fp32 = None
+    if not args.skip_modes:
+        def time_launches(fn, reps):
+            for _ in range(args.warmup):
+                fn()
+            torch.cuda.synchronize(dev)
+            a0 = torch.cuda.Event(enable_timing=True)
+            a1 = torch.cuda.Event(enable_timing=True)
+            a0.record(stream)
+            for _ in range(reps):
+                fn()
+            a1.record(stream)
+            torch.cuda.synchronize(dev)
+            return a0.elapsed_time(a1) / reps
+
+        reps = max(5, min(args.steps, 20))
+        xf = x.float()
+        of = torch.empty((KMAX + 1, n), dtype=torch.float32, device=dev)
+        ms32 = time_launches(lambda: pb.boys_eval_f32(xf, KMAX, out=of), reps)
+        fp32 = {"kmax32_same_args": {"value": n * (KMAX + 1) / (ms32 / 1e3), "unit": UNIT, "ms": ms32,
+                                     "vs_fp64": ms_per_step / ms32,
+                                     "hbm_gbs": n * 4 * (KMAX + 2) / (ms32 / 1e3) / 1e9,
+                                     "hbm_frac": n * 4 * (KMAX + 2) / (ms32 / 1e3) / 1e9 / hbm_gbs}}
+        del xf, of
+        x4 = W.mixture_c1(n, seed=4)
+        x4d = torch.from_numpy(x4).to(dev)
+        x4f = x4d.float()
+        for km in (4, 12, 24):
+            o32 = torch.empty((km + 1, n), dtype=torch.float32, device=dev)
+            o64 = torch.empty((km + 1, n), dtype=torch.float64, device=dev)
+            t32 = time_launches(lambda: pb.boys_eval_f32(x4f, km, out=o32), reps)
+            t64 = time_launches(lambda: pb.boys_eval(x4d, km, out=o64), reps)
+            fp32[f"parity_mix_kmax{km}"] = {
+                "fp32_value": n * (km + 1) / (t32 / 1e3), "fp64_value": n * (km + 1) / (t64 / 1e3),
+                "unit": UNIT, "fp32_ms": t32, "fp64_ms": t64, "speedup": t64 / t32,
+                "fp32_hbm_frac": n * 4 * (km + 2) / (t32 / 1e3) / 1e9 / hbm_gbs}
+            del o32, o64
+        del x4d, x4f
+
     ragged = None
     if not args.skip_modes:
         x3, off3, km3 = W.ragged_c3()
@@ -380,7 +421,7 @@ def run_ours(args):
                        "l2": "inputs larger than L2 (x 0.54 GB read, 17.7 GB written per step); no flush",
                        "parallelism": f"replicas x{ws}, no data-path collective"},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": args.steps,
-            "clocks": clocks, "modes": {"fused_kmax32": fused, "ragged_4096seg": ragged},
+            "clocks": clocks, "modes": {"fused_kmax32": fused, "ragged_4096seg": ragged, "fp32_tier": fp32},
         }
         print(json.dumps(line))
     if dist is not None:

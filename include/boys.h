@@ -85,6 +85,18 @@ boys_status boys_eval_fused(const double* x, const double* rho, int64_t n, int k
                             double* out, void* stream);
 
 /*
+ * FP32 tier: Algorithm 1 in single precision with this library's own rational
+ * minimax tables (generated by a rational Remez code in extended precision,
+ * Section II.B, degrees chosen from the Walsh table as in Section II.D), one
+ * set per kmax: x0(kmax) from Eq. x0, x1(kmax) from Eq. x1 with a 3e-7
+ * asymptotic budget.  Absolute accuracy 1e-6 for every order against the
+ * exact F_k at the (float) input.  x float [n]; out float [kmax+1][ld];
+ * 0 <= kmax <= 32; 16-byte alignment of x and out and ld % 4 == 0 enable
+ * 128-bit accesses.
+ */
+boys_status boys_eval_f32(const float* x, int64_t n, int kmax, float* out, int64_t ld, void* stream);
+
+/*
  * Backward pass: dF_k/dx = -F_{k+1} (Eq. 3 differentiated under the integral
  * sign), so for upstream gradients g_k = dL/dF_k
  *   dx[i] = -sum_{k=0}^{kmax} g[k*ldg + i] * F_{k+1}(x_i).

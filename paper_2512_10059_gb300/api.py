@@ -50,6 +50,22 @@ def boys_eval(x: torch.Tensor, kmax: int, out: torch.Tensor = None, stream=None)
     return out
 
 
+def boys_eval_f32(x: torch.Tensor, kmax: int, out: torch.Tensor = None, stream=None) -> torch.Tensor:
+    """FP32 tier: F_0..F_kmax(x) at 1e-6 absolute accuracy, [kmax+1, n] float32."""
+    _require(x, "x", torch.float32)
+    x = x.contiguous().view(-1)
+    n = x.numel()
+    if out is None:
+        out = torch.empty((kmax + 1, n), dtype=torch.float32, device=x.device)
+    _require(out, "out", torch.float32)
+    if out.dim() != 2 or out.shape[0] != kmax + 1 or out.shape[1] != n or (n > 1 and out.stride(1) != 1):
+        raise ValueError(f"out must be [{kmax + 1}, {n}] with unit column stride")
+    ld = out.stride(0) if kmax > 0 else max(n, 1)
+    st = _lib.lib().boys_eval_f32(x.data_ptr(), n, int(kmax), out.data_ptr(), ld, _stream_handle(x, stream))
+    _lib.check("boys_eval_f32", st)
+    return out
+
+
 def boys_eval_fused(x: torch.Tensor, rho: torch.Tensor, kmax: int, out: torch.Tensor = None,
                     stream=None) -> torch.Tensor:
     """sum_k (-2 rho_i)^k F_k(x_i) for every i, F_k kept in registers."""
