@@ -61,6 +61,14 @@ int boys_version(void);
 int boys_kmax_limit(void);
 
 /*
+ * Diagnostic (no counterpart in the paper): applies one of the library's own
+ * FP64 elementary functions elementwise, out[i] = f(a[i]):
+ *   fn 0: e^{-a} (0 <= a <= 700)  1: 1/a  2: b[i]/a  3: a^{-1/2}   (a normal)
+ * so that their accuracy can be measured against CUDA's functions.
+ */
+boys_status boys_diag_math(int fn, const double* a, const double* b, int64_t n, double* out, void* stream);
+
+/*
  * FP64 stored mode — Algorithm 1 for every x_i.
  *   x    [n]            input arguments (8-byte aligned; 16-byte alignment
  *                       of x, out and an even ld enable 128-bit accesses)

@@ -20,11 +20,14 @@
 //     C:  a_j = 2j+1,    s = 0,        c_j = 1/(2x)
 // Division by 2l+1 is a multiplication by the rounded constant 1/(2l+1); the
 // paper's zeroth-order error analysis (Appendix B) is indifferent to it.
+// Divisions, 1/(2x), x^{-1/2} and e^{-x} use the FP64-lean routines of
+// boys_math.cuh; region tests compare bit patterns on the integer pipes.
 #pragma once
 
 #include <cstdint>
 
 #include "boys_coeffs_fp64.h"
+#include "boys_math.cuh"
 
 namespace boys {
 namespace fp64 {
@@ -52,6 +55,14 @@ struct Degrees {
 
 __device__ __forceinline__ double quiet_nan() { return __longlong_as_double(0x7ff8000000000000LL); }
 
+// Bit patterns of the region boundaries: for non-negative doubles (and +inf)
+// the IEEE order equals the integer order of the bit patterns, so the region
+// tests run on the integer pipes instead of the scarce FP64 pipe.
+constexpr long long kBitsX0 = BOYS_FP64_X0_BITS;
+constexpr long long kBitsX1 = BOYS_FP64_X1_BITS;
+constexpr long long kBitsInf = 0x7FF0000000000000LL;
+constexpr long long kBits1e300 = 0x7E37E43C8800759CLL;  // 1e300
+
 // F_0..F_KMAX (KMAX <= 32) at x; results in F[0..KMAX].
 template <int KMAX>
 __device__ __forceinline__ void eval_point(double x, double (&F)[KMAX + 1]) {
@@ -59,9 +70,12 @@ __device__ __forceinline__ void eval_point(double x, double (&F)[KMAX + 1]) {
     constexpr int NP = Degrees<KMAX>::NP;
     constexpr int NQ = Degrees<KMAX>::NQ;
 
-    x = (x >= 0.0) ? x : quiet_nan();  // x < 0 and NaN -> NaN everywhere
-    const bool inA = x < kX0;
-    const bool inC = x >= kX1;
+    long long xb = __double_as_longlong(x);
+    if (xb == (long long)0x8000000000000000ULL) xb = 0;  // -0.0 -> +0.0
+    const bool valid = xb >= 0 && xb <= kBitsInf;         // x < 0 and NaN -> NaN everywhere
+    x = valid ? __longlong_as_double(xb) : quiet_nan();
+    const bool inA = valid && xb < kBitsX0;
+    const bool inC = !valid || xb >= kBitsX1;
 
     // Anchor: r_{A,KMAX} in A, r_B in B (Horner, monic denominators).
     double p = inA ? c_ra_p[KMAX][NP] : c_rb_p[NP];
@@ -70,12 +84,19 @@ __device__ __forceinline__ void eval_point(double x, double (&F)[KMAX + 1]) {
     double q = inA ? c_ra_q[KMAX][NQ] : c_rb_q[NQ];
 #pragma unroll
     for (int i = NQ - 1; i >= 0; --i) q = fma(q, x, inA ? c_ra_q[KMAX][i] : c_rb_q[i]);
-    const double rat = p / q;
+    const double rat = dmath::div(p, q);
 
-    const double asym0 = kSqrtPiOver2 * rsqrt(x);  // region C anchor
-    const double e = inC ? 0.0 : exp(-x);
+    // Region C anchor and the step factor 1/(2x) of B and C; arguments beyond
+    // 1e300 are clamped there (F_0 < 1e-150 and F_k = 0 for k > 0 either way),
+    // +inf gives exactly 0.
+    const bool huge = xb > kBits1e300 && xb <= kBitsInf;
+    const double xr = huge ? 1e300 : x;
+    const double asym0 = (xb == kBitsInf) ? 0.0 : kSqrtPiOver2 * dmath::rsqrt(xr);
+    const double inv2x = dmath::rcp(xr + xr);
+    const double e = dmath::exp_neg(inC ? 0.0 : x);
     const double two_x = x + x;
-    const double inv2x = 1.0 / two_x;
+    const long long sflip = inA ? 0LL : (long long)0x8000000000000000ULL;  // s = +e in A, -e in B
+    const double s = inC ? 0.0 : __longlong_as_double(__double_as_longlong(e) ^ sflip);
 
     double y[KMAX + 1];
     y[0] = inC ? asym0 : rat;
@@ -84,7 +105,6 @@ __device__ __forceinline__ void eval_point(double x, double (&F)[KMAX + 1]) {
         const int l = KMAX - 1 - j;
         const double a = inA ? two_x : (double)(2 * j + 1);
         const double c = inA ? (1.0 / (double)(2 * l + 1)) : inv2x;
-        const double s = inA ? e : -e;
         y[j + 1] = fma(a, y[j], s) * c;
     }
 #pragma unroll

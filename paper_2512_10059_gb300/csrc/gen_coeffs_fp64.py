@@ -14,6 +14,7 @@ converted by the C library's correctly rounded ``strtod`` semantics (Python
 the header holds exactly the doubles the paper specifies.
 """
 import re
+import struct
 import sys
 
 CAPTION = re.compile(r"\\caption\{Rational minimax coefficients for \$F_\{?(\d+)\}?\$ on \$\[(.*?)\\rangle\$\}")
@@ -75,6 +76,9 @@ def emit(x0, x1, tables, src_name):
     w("#define BOYS_FP64_KMAX 32")
     w(f"#define BOYS_FP64_X0 {float(x0)!r}  /* Appendix D, Eq. value_of_x0 */")
     w(f"#define BOYS_FP64_X1 {float(x1)!r}  /* Appendix D, Eq. value_of_x1 */")
+    # IEEE bit patterns (for integer-pipe region tests on non-negative doubles)
+    w(f"#define BOYS_FP64_X0_BITS 0x{struct.unpack('<q', struct.pack('<d', float(x0)))[0]:016X}LL")
+    w(f"#define BOYS_FP64_X1_BITS 0x{struct.unpack('<q', struct.pack('<d', float(x1)))[0]:016X}LL")
     w("")
     w(f"// r_B: F_0 on [x_0, x_1), (n, m) = ({len(rb['num']) - 1}, {len(rb['den']) - 1})")
     w(f"#define BOYS_RB_N {len(rb['num']) - 1}")

@@ -1,0 +1,58 @@
+"""The library's FP64 elementary functions (Tang exp, Newton reciprocal and
+division, Newton rsqrt) against CUDA's functions and a long double reference."""
+import numpy as np
+import pytest
+import torch
+
+from paper_2512_10059_gb300 import _lib
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+
+
+def _run(fn, a, b=None):
+    L = _lib.lib()
+    at = torch.from_numpy(a).to(DEV)
+    bt = torch.from_numpy(b).to(DEV) if b is not None else None
+    out = torch.empty_like(at)
+    st = L.boys_diag_math(fn, at.data_ptr(), bt.data_ptr() if bt is not None else None, a.size, out.data_ptr(),
+                          int(torch.cuda.current_stream().cuda_stream))
+    _lib.check("boys_diag_math", st)
+    torch.cuda.synchronize()
+    return out.cpu().numpy(), at, bt
+
+
+def _ulps(got, ref_ld):
+    ref = ref_ld.astype(np.float64)
+    spacing = np.spacing(np.abs(ref))
+    return np.abs((got.astype(np.longdouble) - ref_ld) / spacing.astype(np.longdouble)).astype(np.float64)
+
+
+def test_exp_neg():
+    rng = np.random.default_rng(0)
+    a = np.concatenate([rng.uniform(0, 30, 200000), rng.uniform(0, 700, 50000), [0.0, 1e-300, 29.0, 700.0]])
+    got, at, _ = _run(0, a)
+    ref = np.exp(-a.astype(np.longdouble))
+    assert _ulps(got, ref).max() <= 2.0
+    cuda = torch.exp(-at).cpu().numpy()
+    assert np.max(np.abs(got - cuda) / np.spacing(cuda)) <= 2.0
+
+
+@pytest.mark.parametrize("fn", [1, 2, 3])
+def test_reciprocal_division_rsqrt(fn):
+    rng = np.random.default_rng(fn)
+    a = np.exp(rng.uniform(-300, 300, 300000) * np.log(2.0))
+    b = rng.uniform(-1e3, 1e3, a.size) if fn == 2 else None
+    got, at, bt = _run(fn, a, b)
+    A = a.astype(np.longdouble)
+    if fn == 1:
+        ref, cuda = 1 / A, (1.0 / at).cpu().numpy()
+        bound = 1.0
+    elif fn == 2:
+        ref, cuda = b.astype(np.longdouble) / A, (bt / at).cpu().numpy()
+        bound = 1.0
+    else:
+        ref, cuda = 1 / np.sqrt(A), torch.rsqrt(at).cpu().numpy()
+        bound = 1.5
+    assert _ulps(got, ref).max() <= bound
+    assert np.max(np.abs(got - cuda) / np.spacing(np.abs(cuda))) <= bound + 1.0

@@ -11,6 +11,7 @@
 import json
 import math
 import os
+import re
 
 import numpy as np
 import pytest
@@ -115,3 +116,13 @@ def test_algorithm1_host_port_within_eps(H, kmax):
     hi, lo = oracle.boys(x, kmax)
     err = np.abs((F - hi) - lo)
     assert err.max() <= EPS + SLACK, (kmax, err.max(), x[np.unravel_index(err.argmax(), err.shape)[1]])
+
+
+def test_boundary_bit_patterns():
+    """The kernels classify arguments by comparing IEEE bit patterns."""
+    import struct
+    s = open(boys_header.HEADER).read()
+    for name, val in (("X0", 11.899848152108484), ("X1", 28.989337738820740)):
+        bits = int(re.search(rf"#define BOYS_FP64_{name}_BITS 0x([0-9A-F]+)LL", s).group(1), 16)
+        assert bits == struct.unpack("<q", struct.pack("<d", val))[0]
+    assert struct.unpack("<q", struct.pack("<d", 1e300))[0] == 0x7E37E43C8800759C
