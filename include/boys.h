@@ -83,6 +83,18 @@ boys_status boys_eval(const double* x, int64_t n, int kmax, double* out, int64_t
                       void* stream);
 
 /*
+ * FP64 stored mode on HOST buffers: x and out live in host memory that the
+ * GPU can address (pinned with cudaHostAlloc / cudaHostRegister, or pageable
+ * memory on systems with pageable-memory access).  The evaluation kernel
+ * reads x and writes F over the host link itself (on GB300: NVLink-C2C, ~210
+ * GB/s in, ~193 GB/s out, the same as copy engines reach), so no staging
+ * buffer, copy or device allocation is involved.  Same arguments, layout and
+ * results as boys_eval; asynchronous on `stream`; a buffer the GPU cannot
+ * address returns BOYS_ERR_INVALID_ARG.
+ */
+boys_status boys_eval_host(const double* x, int64_t n, int kmax, double* out, int64_t ld, void* stream);
+
+/*
  * FP64 fused consumer — the F_k never leave registers:
  *   out[i] = sum_{k=0}^{kmax} (-2 rho_i)^k F_k(x_i)
  * (the McMurchie-Davidson-style scaling of an electron-repulsion-integral

@@ -33,6 +33,7 @@ def _declare(lib):
         "boys_kmax_limit": (i32, []),
         "boys_diag_math": (i32, [i32, vp, vp, i64, vp, vp]),
         "boys_eval": (i32, [vp, i64, i32, vp, i64, vp]),
+        "boys_eval_host": (i32, [vp, i64, i32, vp, i64, vp]),
         "boys_eval_fused": (i32, [vp, vp, i64, i32, vp, vp]),
         "boys_grad": (i32, [vp, i64, i32, vp, i64, vp, vp]),
         "boys_eval_f32": (i32, [vp, i64, i32, vp, i64, vp]),

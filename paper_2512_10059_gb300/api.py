@@ -50,6 +50,29 @@ def boys_eval(x: torch.Tensor, kmax: int, out: torch.Tensor = None, stream=None)
     return out
 
 
+def boys_eval_host(x: torch.Tensor, kmax: int, out: torch.Tensor = None, stream=None,
+                   device=None) -> torch.Tensor:
+    """F_0..F_kmax for a pinned HOST tensor x, written into a pinned host
+    tensor ``out`` [kmax+1, n] by the kernel over the host link (no device
+    staging).  Asynchronous on the current stream of ``device`` (default
+    cuda:0): synchronise before reading ``out``."""
+    if x.is_cuda or x.dtype != torch.float64:
+        raise TypeError("x must be a float64 CPU tensor (pinned)")
+    x = x.contiguous().view(-1)
+    n = x.numel()
+    if out is None:
+        out = torch.empty((kmax + 1, n), dtype=torch.float64, pin_memory=True)
+    if out.is_cuda or out.dtype != torch.float64 or out.dim() != 2 or out.shape != (kmax + 1, n) \
+            or (n > 1 and out.stride(1) != 1):
+        raise ValueError(f"out must be a float64 CPU tensor [{kmax + 1}, {n}] with unit column stride")
+    dev = torch.device(device) if device is not None else torch.device("cuda", 0)
+    s = stream if stream is not None else torch.cuda.current_stream(dev)
+    ld = out.stride(0) if kmax > 0 else max(n, 1)
+    st = _lib.lib().boys_eval_host(x.data_ptr(), n, int(kmax), out.data_ptr(), ld, int(s.cuda_stream))
+    _lib.check("boys_eval_host", st)
+    return out
+
+
 def boys_eval_f32(x: torch.Tensor, kmax: int, out: torch.Tensor = None, stream=None) -> torch.Tensor:
     """FP32 tier: F_0..F_kmax(x) at 1e-6 absolute accuracy, [kmax+1, n] float32."""
     _require(x, "x", torch.float32)

@@ -110,3 +110,44 @@ BOYS_API boys_status boys_eval_fused(const double* x, const double* rho, int64_t
     fn<<<(unsigned)grid, kBlock, 0, (cudaStream_t)stream>>>(x, rho, n, out);
     return check_cuda(cudaGetLastError(), "boys_eval_fused launch");
 }
+
+// Host buffers (pinned, or pageable where the GPU can address pageable memory):
+// the evaluation kernel itself reads x and writes F over the host link.
+namespace boys {
+static boys_status host_view(const void* p, void** dev, const char* what) {
+    cudaPointerAttributes a;
+    cudaError_t e = cudaPointerGetAttributes(&a, p);
+    if (e != cudaSuccess) return check_cuda(e, "boys_eval_host: cudaPointerGetAttributes");
+    if (a.type == cudaMemoryTypeHost && a.devicePointer) {
+        *dev = a.devicePointer;
+        return BOYS_OK;
+    }
+    if (a.type == cudaMemoryTypeUnregistered) {
+        int device = 0, pageable = 0;
+        cudaGetDevice(&device);
+        cudaDeviceGetAttribute(&pageable, cudaDevAttrPageableMemoryAccess, device);
+        if (pageable) {
+            *dev = const_cast<void*>(p);
+            return BOYS_OK;
+        }
+    }
+    return fail(BOYS_ERR_INVALID_ARG,
+                "boys_eval_host: %s is not host memory the GPU can address (pin it with cudaHostAlloc/cudaHostRegister)",
+                what);
+}
+}  // namespace boys
+
+BOYS_API boys_status boys_eval_host(const double* x, int64_t n, int kmax, double* out, int64_t ld, void* stream) {
+    using namespace boys;
+    if (kmax < 0 || kmax > 32) return fail(BOYS_ERR_KMAX, "boys_eval_host: kmax=%d outside [0, 32]", kmax);
+    if (n < 0) return fail(BOYS_ERR_INVALID_ARG, "boys_eval_host: n=%lld < 0", (long long)n);
+    if (ld < n) return fail(BOYS_ERR_INVALID_ARG, "boys_eval_host: ld=%lld < n=%lld", (long long)ld, (long long)n);
+    if (n == 0) return BOYS_OK;
+    if (!x || !out) return fail(BOYS_ERR_INVALID_ARG, "boys_eval_host: NULL pointer");
+    void *xd = nullptr, *od = nullptr;
+    boys_status st = host_view(x, &xd, "x");
+    if (st != BOYS_OK) return st;
+    st = host_view(out, &od, "out");
+    if (st != BOYS_OK) return st;
+    return boys_eval((const double*)xd, n, kmax, (double*)od, ld, stream);
+}

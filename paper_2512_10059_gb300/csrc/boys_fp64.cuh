@@ -111,5 +111,6 @@ __device__ __forceinline__ void eval_point(double x, double (&F)[KMAX + 1]) {
     for (int k = 0; k <= KMAX; ++k) F[k] = inA ? y[KMAX - k] : y[k];
 }
 
+
 }  // namespace fp64
 }  // namespace boys

@@ -90,3 +90,10 @@ def test_every_declared_function_has_ctypes_signature(L):
     for name in declared_functions():
         assert name in _lib.SIGNATURES, f"{name} has no ctypes signature in _lib"
         assert getattr(L, name).argtypes is not None or _lib.SIGNATURES[name][1] == []
+
+
+def test_eval_host_argument_errors(L):
+    assert L.boys_eval_host(FAKE, 10, 33, FAKE, 10, None) == 2
+    assert L.boys_eval_host(FAKE, 10, 4, FAKE, 9, None) == 1
+    assert L.boys_eval_host(None, 10, 4, FAKE, 10, None) == 1
+    assert L.boys_eval_host(None, 0, 4, None, 0, None) == 0

@@ -163,3 +163,23 @@ def test_argument_errors_on_device():
         pb.boys_eval(xt, 33)
     with pytest.raises(TypeError):
         pb.boys_eval(xt.float(), 4)
+
+
+def test_host_buffers_zero_copy():
+    """boys_eval_host on pinned host tensors: the kernel reads and writes host
+    memory over the link; results are bitwise those of boys_eval."""
+    x = W.mixture_c2(100003, seed=17)
+    xh = torch.from_numpy(x).pin_memory()
+    out = pb.boys_eval_host(xh, 32)
+    ref = pb.boys_eval(torch.from_numpy(x).to(DEV), 32)
+    torch.cuda.synchronize()
+    assert torch.equal(out, ref.cpu())
+    # pageable memory works only where the GPU can address it; otherwise a clean error
+    xp = torch.from_numpy(x[:1000].copy())
+    op = torch.empty((33, 1000), dtype=torch.float64)
+    try:
+        pb.boys_eval_host(xp, 32, out=op)
+        torch.cuda.synchronize()
+        assert torch.equal(op, ref[:, :1000].cpu())
+    except pb._lib.BoysError as exc:
+        assert exc.status == 1
