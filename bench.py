@@ -343,6 +343,22 @@ def run_ours(args):
             del o32, o64
         del x4d, x4f
 
+    # backward: N = 2^24 (2^(n_log2 - 2) when profiling), kmax = 16, x log-uniform
+    # [1e-10, 1e3], upstream gradients N(0,1) drawn on the device (seeded)
+    grad = None
+    if not args.skip_modes:
+        ng = n >> 2
+        kg = 16
+        xg = torch.from_numpy(W.log_uniform(W.uniform01(W.stream_key(5, 1), ng), 1e-10, 1e3)).to(dev)
+        gen = torch.Generator(device=dev)
+        gen.manual_seed(6)
+        gg = torch.randn((kg + 1, ng), dtype=torch.float64, device=dev, generator=gen)
+        dxg = torch.empty(ng, dtype=torch.float64, device=dev)
+        gms = time_launches(lambda: pb.boys_grad(xg, gg, kg, out=dxg), max(5, min(args.steps, 20)))
+        grad = {"value": ng * (kg + 1) / (gms / 1e3), "unit": "dL/dF_k terms/s", "ms": gms, "n": ng, "kmax": kg,
+                "hbm_gbs": ng * 8 * (kg + 3) / (gms / 1e3) / 1e9}
+        del xg, gg, dxg
+
     ragged = None
     if not args.skip_modes:
         x3, off3, km3 = W.ragged_c3()
@@ -424,7 +440,7 @@ def run_ours(args):
                        "l2": "inputs larger than L2 (x 0.54 GB read, 17.7 GB written per step); no flush",
                        "parallelism": f"replicas x{ws}, no data-path collective"},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": args.steps,
-            "clocks": clocks, "modes": {"fused_kmax32": fused, "ragged_4096seg": ragged, "fp32_tier": fp32},
+            "clocks": clocks, "modes": {"fused_kmax32": fused, "ragged_4096seg": ragged, "fp32_tier": fp32, "grad_kmax16": grad},
         }
         print(json.dumps(line))
     if dist is not None:
