@@ -51,7 +51,7 @@ HBM_FALLBACK_GBS = 6800.0
 # DRAM bytes per argument of the timed kernel from one ncu capture at N = 2^22
 # (profiles/k_eval_f64_kmax32_eri_mixture.md), scaled to the launch by the
 # arguments it processes; None whenever the kernel changed since that capture.
-TRAFFIC_BYTES_PER_X = 257.5
+TRAFFIC_BYTES_PER_X = 259.2
 
 
 def peaks():
@@ -273,7 +273,7 @@ def run_ours(args):
                 "unit": "GB/s", "peak_source": f"{hbm_src} copy bandwidth"}
     roof["frac"] = roof["achieved"] / roof["peak"]
     roof["traffic"] = None if TRAFFIC_BYTES_PER_X is None else TRAFFIC_BYTES_PER_X * n
-    roof["kernel"] = "k_eval_f64<32,2>"
+    roof["kernel"] = "k_eval_f64<32>"
     roof["algorithmic_flops_per_x"] = fpx
     roof["algorithmic_bytes_per_x"] = 8 * (KMAX + 2)
     roof["hbm_frac"] = bytes_per_launch / avg_launch_s / 1e9 / hbm_gbs

@@ -1,45 +1,32 @@
 // FP64 stored mode (boys_eval) and fused consumer (boys_eval_fused).
 //
-// One thread evaluates XPT consecutive arguments (XPT = 2 uses 128-bit loads
-// of x and 128-bit streaming stores of each order's pair), keeps
-// F_0..F_KMAX in registers (KMAX is a template parameter, so every loop is
-// unrolled) and writes order-major rows: a warp's store of one order covers
-// 32*XPT consecutive doubles.  Grid-stride loop, grid capped at a few waves
-// of resident blocks.
+// Stored mode: one thread per argument (grid-stride loop, grid capped at a few
+// waves of resident blocks); KMAX is a template parameter so every loop is
+// unrolled; each order is written to its order-major row as soon as the
+// recurrence produces it, which keeps the register count low enough for the
+// occupancy that hides the integer-pipe latency of the recurrence.
 #include <array>
 #include <utility>
 
 #include "boys_fp64.cuh"
 #include "boys_internal.h"
 
+// Minimum resident blocks per SM for the stored-mode kernel (caps registers).
+#ifndef BOYS_STORED_MIN_BLOCKS
+#define BOYS_STORED_MIN_BLOCKS 8
+#endif
+
 namespace boys {
 namespace {
 
 constexpr int kBlock = 128;
 
-template <int KMAX, int XPT>
-__global__ void __launch_bounds__(kBlock) k_eval_f64(const double* __restrict__ x, int64_t n,
+template <int KMAX>
+__global__ void __launch_bounds__(kBlock, BOYS_STORED_MIN_BLOCKS) k_eval_f64(const double* __restrict__ x, int64_t n,
                                                      double* __restrict__ out, int64_t ld) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t * XPT < n; t += stride) {
-        const int64_t i0 = t * XPT;
-        if (XPT == 2 && i0 + 2 <= n) {
-            const double2 xv = __ldcs(reinterpret_cast<const double2*>(x + i0));
-            double F0[KMAX + 1], F1[KMAX + 1];
-            fp64::eval_point<KMAX>(xv.x, F0);
-            fp64::eval_point<KMAX>(xv.y, F1);
-#pragma unroll
-            for (int k = 0; k <= KMAX; ++k)
-                __stcs(reinterpret_cast<double2*>(out + k * ld + i0), make_double2(F0[k], F1[k]));
-        } else {
-            for (int j = 0; j < XPT && i0 + j < n; ++j) {
-                double F[KMAX + 1];
-                fp64::eval_point<KMAX>(__ldcs(x + i0 + j), F);
-#pragma unroll
-                for (int k = 0; k <= KMAX; ++k) __stcs(out + k * ld + i0 + j, F[k]);
-            }
-        }
-    }
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+        fp64::eval_store<KMAX>(__ldcs(x + i), out + i, ld);
 }
 
 // out[i] = sum_k (-2 rho_i)^k F_k(x_i), by Horner in a = -2 rho from F_KMAX down.
@@ -59,10 +46,10 @@ __global__ void __launch_bounds__(kBlock) k_fused_f64(const double* __restrict__
     }
 }
 
-template <int XPT, int... K>
+template <int... K>
 constexpr auto eval_table(std::integer_sequence<int, K...>) {
     using Fn = void (*)(const double*, int64_t, double*, int64_t);
-    return std::array<Fn, sizeof...(K)>{&k_eval_f64<K, XPT>...};
+    return std::array<Fn, sizeof...(K)>{&k_eval_f64<K>...};
 }
 
 template <int... K>
@@ -85,12 +72,10 @@ BOYS_API boys_status boys_eval(const double* x, int64_t n, int kmax, double* out
     if (!x || !out) return fail(BOYS_ERR_INVALID_ARG, "boys_eval: NULL pointer");
     if (ld > INT64_MAX / (kmax + 1)) return fail(BOYS_ERR_INVALID_ARG, "boys_eval: (kmax+1)*ld overflows");
     if (!aligned(x, 8) || !aligned(out, 8)) return fail(BOYS_ERR_ALIGNMENT, "boys_eval: x/out not 8-byte aligned");
-    static constexpr auto t1 = eval_table<1>(std::make_integer_sequence<int, 33>{});
-    static constexpr auto t2 = eval_table<2>(std::make_integer_sequence<int, 33>{});
-    const bool vec = aligned(x, 16) && aligned(out, 16) && (ld % 2 == 0);
-    const auto fn = vec ? t2[kmax] : t1[kmax];
-    const int xpt = vec ? 2 : 1;
-    const int64_t grid = grid_for((const void*)fn, kBlock, n, (int64_t)kBlock * xpt);
+    // one argument per thread, each order stored as soon as it is produced
+    static constexpr auto t1 = eval_table(std::make_integer_sequence<int, 33>{});
+    const auto fn = t1[kmax];
+    const int64_t grid = grid_for((const void*)fn, kBlock, n, (int64_t)kBlock);
     fn<<<(unsigned)grid, kBlock, 0, (cudaStream_t)stream>>>(x, n, out, ld);
     return check_cuda(cudaGetLastError(), "boys_eval launch");
 }

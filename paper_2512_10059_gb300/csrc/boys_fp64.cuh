@@ -28,9 +28,18 @@
 
 #include "boys_coeffs_fp64.h"
 #include "boys_math.cuh"
+#include "boys_xf.cuh"
 
 namespace boys {
 namespace fp64 {
+
+// Recurrence steps that run in FP64; the rest use the 64-bit-significand
+// integer format (boys_xf.cuh).  Splitting the steps balances the FP64 pipe
+// (anchors, e^{-x}, reciprocals and these steps) against the integer pipes;
+// 8 was fastest in a sweep over 0..12 on GB300 (kmax = 32 stored mode).
+#ifndef BOYS_FP64_STEPS
+#define BOYS_FP64_STEPS 8
+#endif
 
 constexpr int kRaN[33] = BOYS_RA_N_INIT;
 constexpr int kRaM[33] = BOYS_RA_M_INIT;
@@ -63,9 +72,15 @@ constexpr long long kBitsX1 = BOYS_FP64_X1_BITS;
 constexpr long long kBitsInf = 0x7FF0000000000000LL;
 constexpr long long kBits1e300 = 0x7E37E43C8800759CLL;  // 1e300
 
-// F_0..F_KMAX (KMAX <= 32) at x; results in F[0..KMAX].
+// Everything Algorithm 1 needs before the recurrence, for one argument.
+struct Setup {
+    bool valid, inA;
+    double y0d, two_x, sd, inv2x;   // FP64 anchor, 2x, s = +-e^{-x} (0 in C), 1/(2x)
+    xf::Xf y0, X2, Ev, R;           // the same in the 64-bit-significand format
+};
+
 template <int KMAX>
-__device__ __forceinline__ void eval_point(double x, double (&F)[KMAX + 1]) {
+__device__ __forceinline__ Setup setup(double x) {
     static_assert(KMAX >= 0 && KMAX <= 32, "tables cover orders 0..32");
     constexpr int NP = Degrees<KMAX>::NP;
     constexpr int NQ = Degrees<KMAX>::NQ;
@@ -94,23 +109,106 @@ __device__ __forceinline__ void eval_point(double x, double (&F)[KMAX + 1]) {
     const double asym0 = (xb == kBitsInf) ? 0.0 : kSqrtPiOver2 * dmath::rsqrt(xr);
     const double inv2x = dmath::rcp(xr + xr);
     const double e = dmath::exp_neg(inC ? 0.0 : x);
-    const double two_x = x + x;
-    const long long sflip = inA ? 0LL : (long long)0x8000000000000000ULL;  // s = +e in A, -e in B
-    const double s = inC ? 0.0 : __longlong_as_double(__double_as_longlong(e) ^ sflip);
 
-    double y[KMAX + 1];
-    y[0] = inC ? asym0 : rat;
-#pragma unroll
-    for (int j = 0; j < KMAX; ++j) {
-        const int l = KMAX - 1 - j;
-        const double a = inA ? two_x : (double)(2 * j + 1);
-        const double c = inA ? (1.0 / (double)(2 * l + 1)) : inv2x;
-        y[j + 1] = fma(a, y[j], s) * c;
-    }
-#pragma unroll
-    for (int k = 0; k <= KMAX; ++k) F[k] = inA ? y[KMAX - k] : y[k];
+    Setup S;
+    S.valid = valid;
+    S.inA = inA;
+    S.y0d = inC ? asym0 : rat;
+    S.two_x = x + x;
+    S.sd = inC ? 0.0 : (inA ? e : -e);
+    S.inv2x = inv2x;
+    S.y0 = xf::from_double(S.y0d);
+    S.X2 = xf::from_double(x);
+    S.X2.e += 1;                                     // 2x, exact
+    S.Ev = xf::from_double(inC ? 0.0 : e);           // zero in region C
+    S.R = xf::from_double(inv2x);
+    return S;
 }
 
+// One step y_{j+1} = (a_j y_j + s) c_j of the unified recurrence, in the
+// 64-bit-significand format of boys_xf.cuh on the integer pipes:
+//   A: a_j = 2x, s = +e^{-x}, c_j = 1/(2l+1), l = KMAX-1-j  (y_j = F_{KMAX-j})
+//   B: a_j = 2j+1, s = -e^{-x}, c_j = 1/(2x)                (y_j = F_j)
+//   C: a_j = 2j+1, s = 0,        c_j = 1/(2x)
+template <int KMAX>
+__device__ __forceinline__ xf::Xf step(const Setup& S, int j, xf::Xf y) {
+    const int l = KMAX - 1 - j;
+    const xf::Xf a = xf::select(S.inA, S.X2, xf::odd(j));
+    const xf::Xf c = xf::select(S.inA, xf::recip_odd(l), S.R);
+    return xf::mul(xf::add_signed(xf::mul(a, y), S.Ev, !S.inA), c);
+}
+
+__device__ __forceinline__ double out_value(const Setup& S, xf::Xf y) {
+    return S.valid ? xf::to_double(y) : quiet_nan();
+}
+
+// The same step in FP64 (y_{j+1} = fma(a_j, y_j, s) * c_j).
+template <int KMAX>
+__device__ __forceinline__ double step_fp64(const Setup& S, int j, double y) {
+    const int l = KMAX - 1 - j;
+    const double a = S.inA ? S.two_x : (double)(2 * j + 1);
+    const double c = S.inA ? (1.0 / (double)(2 * l + 1)) : S.inv2x;
+    return fma(a, y, S.sd) * c;
+}
+
+// Value number p of the recurrence (p = 0: the anchor; FP64 for p <= NF64,
+// the integer format after), advancing yd / y in place.
+template <int KMAX, int NSTEPS_FP64 = BOYS_FP64_STEPS>
+__device__ __forceinline__ double next_value(const Setup& S, int p, double& yd, xf::Xf& y) {
+    constexpr int NF64 = NSTEPS_FP64 < KMAX ? NSTEPS_FP64 : KMAX;
+    if (p <= NF64) {
+        if (p > 0) yd = step_fp64<KMAX>(S, p - 1, yd);
+        return S.valid ? yd : quiet_nan();
+    }
+    y = step<KMAX>(S, p - 1, p - 1 == NF64 ? xf::from_double(yd) : y);
+    return out_value(S, y);
+}
+
+// F_0..F_KMAX (KMAX <= 32) at x; results in F[0..KMAX].  NSTEPS_FP64 lets a
+// caller whose own work already loads the FP64 pipe move more steps to the
+// integer format; stored and ragged modes use the default and agree bitwise.
+template <int KMAX, int NSTEPS_FP64 = BOYS_FP64_STEPS>
+__device__ __forceinline__ void eval_point(double x, double (&F)[KMAX + 1]) {
+    const Setup S = setup<KMAX>(x);
+    double yd = S.y0d;
+    xf::Xf y = S.y0;
+    double v[KMAX + 1];
+#pragma unroll
+    for (int p = 0; p <= KMAX; ++p) v[p] = next_value<KMAX, NSTEPS_FP64>(S, p, yd, y);
+#pragma unroll
+    for (int k = 0; k <= KMAX; ++k) F[k] = S.inA ? v[KMAX - k] : v[k];
+}
+
+// Same values, stored by the whole warp one full row at a time: F_k(x) to
+// col[k * ld].  Value number p of the recurrence (p = 0 is the anchor) is
+// F_{KMAX-p} on an A lane and F_p on a B or C lane, so row k is complete once
+// both p = k and p = KMAX-k have been produced.  A lane therefore keeps its
+// values p < KMAX/2 (at most 17 doubles); from p >= KMAX/2 on, step p
+// completes rows p and KMAX-p for every lane of the warp and both are written
+// with coalesced full-line stores (a store that covered only the A lanes or
+// only the B/C lanes of a row would leave partly written sectors, which L2
+// evicts and DRAM then read-modify-writes).
+template <int KMAX>
+__device__ __forceinline__ void eval_store(double x, double* __restrict__ col, int64_t ld) {
+    constexpr int H = KMAX / 2 + 1;
+    const Setup S = setup<KMAX>(x);
+    double hold[H];
+    double yd = S.y0d;
+    xf::Xf y = S.y0;
+#pragma unroll
+    for (int p = 0; p <= KMAX; ++p) {
+        const double v = next_value<KMAX>(S, p, yd, y);
+        if (2 * p < KMAX) {
+            hold[p] = v;
+        } else if (2 * p == KMAX) {
+            __stcs(col + p * ld, v);
+        } else {
+            const int q = KMAX - p;
+            __stcs(col + p * ld, S.inA ? hold[q] : v);
+            __stcs(col + q * ld, S.inA ? v : hold[q]);
+        }
+    }
+}
 
 }  // namespace fp64
 }  // namespace boys

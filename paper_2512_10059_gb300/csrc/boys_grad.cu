@@ -23,7 +23,7 @@ __global__ void __launch_bounds__(kBlock) k_grad_f64(const double* __restrict__ 
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
         double F[KMAX + 2];
-        fp64::eval_point<KMAX + 1>(__ldcs(x + i), F);
+        fp64::eval_point<KMAX + 1, 0>(__ldcs(x + i), F);  // the g_k F_{k+1} sum is FP64 work already
         double s = 0.0;
 #pragma unroll
         for (int k = 0; k <= KMAX; ++k) s = fma(__ldcs(g + k * ldg + i), F[k + 1], s);
