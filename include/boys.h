@@ -184,6 +184,18 @@ boys_status boys_ragged_plan_config(const boys_ragged_plan* plan, int* block, in
 void boys_ragged_plan_destroy(boys_ragged_plan* plan);
 
 /*
+ * The paper's benchmark workload (Section III, Algorithm 2):
+ *   z[i] = sum_{l=0}^{k} c[l] * sum_{j=0}^{n-1} F_l(x[i] + x[j]) * y[j]
+ * for every i, F_l by the three-region Algorithm 1 in FP64 accuracy.
+ *   x, y, z [n]; c [k+1]; 0 <= k <= 32; n <= 2^40.
+ * Work is n^2 (k+1) evaluations.  Sorting x ascending (permuting y alongside)
+ * keeps each warp's arguments in one region and is several times faster; the
+ * result is the same up to summation rounding.
+ */
+boys_status boys_pairwise(const double* x, const double* y, int64_t n, const double* c, int k, double* z,
+                          void* stream);
+
+/*
  * Ragged batch that allocates nothing.  The paper has no counterpart; this is
  * for callers that cannot provide device memory of their own, e.g. code that
  * must not call cudaMalloc because a framework or an application's fixed

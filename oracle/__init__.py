@@ -39,9 +39,15 @@ class OracleLib:
         lib.oracle_grad_batch.argtypes = [_c_double_p, ctypes.c_int64, ctypes.c_int,
                                           _c_double_p, ctypes.c_int64,
                                           _c_double_p, _c_double_p, ctypes.c_int]
+        lib.oracle_pairwise_rows.argtypes = [_c_double_p, _c_double_p, ctypes.c_int64, _c_double_p, ctypes.c_int,
+                                             ctypes.POINTER(ctypes.c_int64), ctypes.c_int64, _c_double_p, _c_double_p,
+                                             ctypes.c_int]
+        lib.oracle_pairwise_rows.restype = ctypes.c_int
+        lib.oracle_pairwise.argtypes = [_c_double_p, _c_double_p, ctypes.c_int64, _c_double_p, ctypes.c_int,
+                                        _c_double_p, _c_double_p, ctypes.c_int]
         for name in ("oracle_boys_branch", "oracle_boys_batch", "oracle_fused_batch",
                      "oracle_grad_batch", "oracle_kmax_limit", "oracle_mantissa_bits",
-                     "oracle_max_threads"):
+                     "oracle_max_threads", "oracle_pairwise"):
             getattr(lib, name).restype = ctypes.c_int
         self._lib = lib
         self.path = path
@@ -103,6 +109,36 @@ class OracleLib:
             raise ValueError(f"oracle_grad_batch rejected kmax={kmax}")
         return hi, lo
 
+    def pairwise(self, x, y, c, nthreads: int = 0):
+        """z_i = sum_l c_l sum_j F_l(x_i + x_j) y_j in binary128: (hi, lo) [n]."""
+        x = np.ascontiguousarray(np.asarray(x, dtype=np.float64).ravel())
+        y = np.ascontiguousarray(np.asarray(y, dtype=np.float64).ravel())
+        c = np.ascontiguousarray(np.asarray(c, dtype=np.float64).ravel())
+        if y.size != x.size:
+            raise ValueError("x and y differ in length")
+        n = x.size
+        hi = np.empty(n)
+        lo = np.empty(n)
+        rc = self._lib.oracle_pairwise(_ptr(x), _ptr(y), n, _ptr(c), c.size - 1, _ptr(hi), _ptr(lo), nthreads)
+        if rc != 0:
+            raise ValueError("oracle_pairwise rejected its arguments")
+        return hi, lo
+
+    def pairwise_rows(self, x, y, c, rows, nthreads: int = 0):
+        """z_i for the given rows only: (hi, lo) [len(rows)]."""
+        x = np.ascontiguousarray(np.asarray(x, dtype=np.float64).ravel())
+        y = np.ascontiguousarray(np.asarray(y, dtype=np.float64).ravel())
+        c = np.ascontiguousarray(np.asarray(c, dtype=np.float64).ravel())
+        rows = np.ascontiguousarray(np.asarray(rows, dtype=np.int64).ravel())
+        hi = np.empty(rows.size)
+        lo = np.empty(rows.size)
+        rc = self._lib.oracle_pairwise_rows(_ptr(x), _ptr(y), x.size, _ptr(c), c.size - 1,
+                                            rows.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), rows.size,
+                                            _ptr(hi), _ptr(lo), nthreads)
+        if rc != 0:
+            raise ValueError("oracle_pairwise_rows rejected its arguments")
+        return hi, lo
+
 
 _default = None
 
@@ -129,6 +165,14 @@ def fused(x, rho, kmax, nthreads=0):
 
 def grad(x, g, kmax, nthreads=0):
     return default().grad(x, g, kmax, nthreads)
+
+
+def pairwise(x, y, c, nthreads=0):
+    return default().pairwise(x, y, c, nthreads)
+
+
+def pairwise_rows(x, y, c, rows, nthreads=0):
+    return default().pairwise_rows(x, y, c, rows, nthreads)
 
 
 def kmax_limit():

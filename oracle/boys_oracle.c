@@ -207,3 +207,49 @@ int oracle_grad_batch(const double* x, int64_t n, int kmax, const double* g, int
     }
     return err ? -1 : 0;
 }
+
+/*
+ * Pairwise benchmark of the paper (Section III, Algorithm 2, Eq. benchmarkequation):
+ *   z_i = sum_{l=0}^{k} c_l sum_{j=0}^{n-1} F_l(x_i + x_j) y_j,
+ * every F_l and every sum in binary128.  O(n^2 k): small n only.
+ */
+int oracle_pairwise(const double* x, const double* y, int64_t n, const double* c, int k,
+                    double* z_hi, double* z_lo, int nthreads) {
+    if (k < 0 || k > ORACLE_KMAX || n < 0) return -1;
+    int err = 0;
+#pragma omp parallel for schedule(dynamic, 4) num_threads(oracle_threads(nthreads)) reduction(| : err)
+    for (int64_t i = 0; i < n; ++i) {
+        qreal f[ORACLE_KMAX + 1];
+        qreal z = QL(0.0);
+        for (int64_t j = 0; j < n; ++j) {
+            if (boys_q(x[i] + x[j], k, 0, f)) { err |= 1; break; }
+            qreal w = QL(0.0);
+            for (int l = 0; l <= k; ++l) w += (qreal)c[l] * f[l];
+            z += w * (qreal)y[j];
+        }
+        q_split(z, &z_hi[i], &z_lo[i]);
+    }
+    return err ? -1 : 0;
+}
+
+/* The same for selected rows only: z[r] = z_{rows[r]}, r < nrows (n may be large). */
+int oracle_pairwise_rows(const double* x, const double* y, int64_t n, const double* c, int k,
+                         const int64_t* rows, int64_t nrows, double* z_hi, double* z_lo, int nthreads) {
+    if (k < 0 || k > ORACLE_KMAX || n < 0 || nrows < 0) return -1;
+    int err = 0;
+    for (int64_t r = 0; r < nrows; ++r) {
+        const int64_t i = rows[r];
+        if (i < 0 || i >= n) return -1;
+        qreal z = QL(0.0);
+#pragma omp parallel for schedule(dynamic, 256) num_threads(oracle_threads(nthreads)) reduction(+ : z) reduction(| : err)
+        for (int64_t j = 0; j < n; ++j) {
+            qreal f[ORACLE_KMAX + 1];
+            if (boys_q(x[i] + x[j], k, 0, f)) { err |= 1; continue; }
+            qreal w = QL(0.0);
+            for (int l = 0; l <= k; ++l) w += (qreal)c[l] * f[l];
+            z += w * (qreal)y[j];
+        }
+        q_split(z, &z_hi[r], &z_lo[r]);
+    }
+    return err ? -1 : 0;
+}

@@ -154,6 +154,27 @@ def boys(x: torch.Tensor, kmax: int) -> torch.Tensor:
     return BoysFunction.apply(x, kmax)
 
 
+def boys_pairwise(x: torch.Tensor, y: torch.Tensor, c: torch.Tensor, out: torch.Tensor = None,
+                  stream=None) -> torch.Tensor:
+    """z_i = sum_l c_l sum_j F_l(x_i + x_j) y_j (the paper's Algorithm 2);
+    k = len(c) - 1.  Sort x ascending (with y) for speed."""
+    for t, name in ((x, "x"), (y, "y"), (c, "c")):
+        _require(t, name)
+    x = x.contiguous().view(-1)
+    y = y.contiguous().view(-1)
+    c = c.contiguous().view(-1)
+    if y.numel() != x.numel():
+        raise ValueError("x and y must have the same length")
+    n = x.numel()
+    if out is None:
+        out = torch.empty(n, dtype=torch.float64, device=x.device)
+    _require(out, "out")
+    st = _lib.lib().boys_pairwise(x.data_ptr(), y.data_ptr(), n, c.data_ptr(), c.numel() - 1, out.data_ptr(),
+                                  _stream_handle(x, stream))
+    _lib.check("boys_pairwise", st)
+    return out
+
+
 # ----------------------------------------------------------------- ragged
 
 PLAN_AUTOTUNE = 1

@@ -125,6 +125,67 @@ __device__ __forceinline__ Setup setup(double x) {
     return S;
 }
 
+// Region-restricted set-up, for warps whose lanes all lie in one region R
+// (0 = A, 1 = B, 2 = C): only that region's anchor and special functions are
+// evaluated.  x must be valid (the caller classifies first).
+enum Region { kRegionA = 0, kRegionB = 1, kRegionC = 2, kRegionNone = 3 };
+
+__device__ __forceinline__ int region_of(double x) {
+    long long xb = __double_as_longlong(x);
+    if (xb == (long long)0x8000000000000000ULL) xb = 0;
+    if (!(xb >= 0 && xb <= kBitsInf)) return kRegionNone;  // x < 0 or NaN
+    return xb < kBitsX0 ? kRegionA : (xb < kBitsX1 ? kRegionB : kRegionC);
+}
+
+template <int R, int KMAX>
+__device__ __forceinline__ Setup setup_region(double x) {
+    Setup S;
+    S.valid = true;
+    S.inA = (R == kRegionA);
+    x = fabs(x);  // -0.0 -> +0.0 (x >= 0 here)
+    if (R == kRegionC) {
+        const long long xb = __double_as_longlong(x);
+        const bool huge = xb > kBits1e300;
+        const double xr = huge ? 1e300 : x;
+        S.y0d = (xb == kBitsInf) ? 0.0 : kSqrtPiOver2 * dmath::rsqrt(xr);
+        S.inv2x = dmath::rcp(xr + xr);
+        S.sd = 0.0;
+        S.Ev = xf::zero();
+    } else {
+        constexpr int N = R == kRegionA ? kRaN[KMAX] : BOYS_RB_N;
+        constexpr int M = R == kRegionA ? kRaM[KMAX] : BOYS_RB_M;
+        double p = R == kRegionA ? c_ra_p[KMAX][N] : c_rb_p[N];
+#pragma unroll
+        for (int i = N - 1; i >= 0; --i) p = fma(p, x, R == kRegionA ? c_ra_p[KMAX][i] : c_rb_p[i]);
+        double q = R == kRegionA ? c_ra_q[KMAX][M] : c_rb_q[M];
+#pragma unroll
+        for (int i = M - 1; i >= 0; --i) q = fma(q, x, R == kRegionA ? c_ra_q[KMAX][i] : c_rb_q[i]);
+        S.y0d = dmath::div(p, q);
+        const double e = dmath::exp_neg(x);
+        S.sd = R == kRegionA ? e : -e;
+        S.inv2x = R == kRegionB ? dmath::rcp(x + x) : 0.0;
+        S.Ev = xf::from_double(e);
+    }
+    S.two_x = x + x;
+    S.y0 = xf::from_double(S.y0d);
+    S.X2 = xf::from_double(x);
+    S.X2.e += 1;
+    S.R = xf::from_double(S.inv2x);
+    return S;
+}
+
+// Warp-level choice of set-up: the region-restricted one when every lane of
+// the warp is in the same region, the branch-free one otherwise.  All 32
+// lanes must call it together.
+template <int KMAX>
+__device__ __forceinline__ Setup setup_warp(double x) {
+    const int r = region_of(x);
+    if (__all_sync(0xffffffffu, r == kRegionA)) return setup_region<kRegionA, KMAX>(x);
+    if (__all_sync(0xffffffffu, r == kRegionB)) return setup_region<kRegionB, KMAX>(x);
+    if (__all_sync(0xffffffffu, r == kRegionC)) return setup_region<kRegionC, KMAX>(x);
+    return setup<KMAX>(x);
+}
+
 // One step y_{j+1} = (a_j y_j + s) c_j of the unified recurrence, in the
 // 64-bit-significand format of boys_xf.cuh on the integer pipes:
 //   A: a_j = 2x, s = +e^{-x}, c_j = 1/(2l+1), l = KMAX-1-j  (y_j = F_{KMAX-j})

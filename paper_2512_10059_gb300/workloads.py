@@ -171,3 +171,15 @@ def small_parity_set(seed: int = 11):
     u = uniform01(stream_key(seed, 1), 64)
     pts.extend(list(log_uniform(u, 1e-12, 1e4)))
     return np.array(pts)
+
+
+def pairwise_alg2(n: int = 1 << 17, k: int = 12, seed: int = 8, sort: bool = True):
+    """The paper's benchmark inputs (Section III): x uniform on [0, 30], y and
+    c standard normal.  Returns (x, y, c); with ``sort`` the x are ascending
+    (y drawn per sorted position, so the set of pairs is unchanged in law)."""
+    x = 30.0 * uniform01(stream_key(seed, 1), n)
+    if sort:
+        x = np.sort(x)
+    y = normal(stream_key(seed, 2), n)
+    c = normal(stream_key(seed, 3), k + 1)
+    return np.ascontiguousarray(x), np.ascontiguousarray(y), np.ascontiguousarray(c)

@@ -188,6 +188,32 @@ def pin_grad_quadrature(o):
             assert abs(q - v) <= 1e-13 * np.abs(gj).sum(), (x, K, q, v)
 
 
+def pin_pairwise_reduces_to_boys(o):
+    """Algorithm 2 with one-hot c and y is a single Boys value:
+    c = e_l, y = e_m  =>  z_i = F_l(x_i + x_m); and z is linear in c and y."""
+    rng = np.random.default_rng(3)
+    x = rng.uniform(0, 30, 9)
+    k = 5
+    for l, m in [(0, 0), (3, 4), (5, 8)]:
+        c = np.zeros(k + 1)
+        c[l] = 1.0
+        y = np.zeros(9)
+        y[m] = 1.0
+        zh, zl = o.pairwise(x, y, c)
+        fh, fl = o.boys(x + x[m], k)
+        assert np.all(np.abs((zh - fh[l]) + (zl - fl[l])) <= 1e-30 * np.abs(fh[l]) + 1e-300), (l, m)
+    yy = rng.standard_normal(9)
+    cc = rng.standard_normal(k + 1)
+    full = o.pairwise(x, yy, cc)
+    part = o.pairwise_rows(x, yy, cc, [2, 7])
+    assert np.array_equal(full[0][[2, 7]], part[0])
+    c1, c2 = rng.standard_normal(k + 1), rng.standard_normal(k + 1)
+    y = rng.standard_normal(9)
+    a = o.pairwise(x, y, c1)[0] + o.pairwise(x, y, c2)[0]
+    b = o.pairwise(x, y, c1 + c2)[0]
+    assert np.max(np.abs(a - b)) <= 1e-14 * np.max(np.abs(b))
+
+
 def pin_x1_golden(o):
     """Appendix D prints x_1 = 28.989337738820740 as the root of Eq. x1 for
     k_max = 32, eps_tol = 5e-14: Gamma(32.5, x1) / (2 x1^32.5) = eps_tol, i.e.
@@ -206,5 +232,5 @@ def pin_x1_golden(o):
 
 CPU_PINS = [pin_at_zero, pin_f0_closed_form, pin_recurrence_identity, pin_branch_overlap,
             pin_derivative, pin_bounds_monotone, pin_quadrature, pin_fused_quadrature,
-            pin_grad_quadrature, pin_x1_golden]
+            pin_grad_quadrature, pin_x1_golden, pin_pairwise_reduces_to_boys]
 MP_PINS = [pin_f0_closed_form_mp, pin_gammainc_mp]

@@ -97,3 +97,10 @@ def test_eval_host_argument_errors(L):
     assert L.boys_eval_host(FAKE, 10, 4, FAKE, 9, None) == 1
     assert L.boys_eval_host(None, 10, 4, FAKE, 10, None) == 1
     assert L.boys_eval_host(None, 0, 4, None, 0, None) == 0
+
+
+def test_pairwise_argument_errors(L):
+    assert L.boys_pairwise(FAKE, FAKE, 10, FAKE, 33, FAKE, None) == 2
+    assert L.boys_pairwise(FAKE, FAKE, -1, FAKE, 3, FAKE, None) == 1
+    assert L.boys_pairwise(FAKE, None, 10, FAKE, 3, FAKE, None) == 1
+    assert L.boys_pairwise(None, None, 0, None, 3, None, None) == 0

@@ -28,6 +28,10 @@ MUTANTS = {
     "fused_sign": ("qreal a = QL(-2.0) * (qreal)rho[i]", "qreal a = QL(2.0) * (qreal)rho[i]"),
     "grad_order_index": ("* f[k + 1];", "* f[k];"),
     "grad_sign": ("q_split(-s, &d_hi[i], &d_lo[i]);", "q_split(s, &d_hi[i], &d_lo[i]);"),
+    "pairwise_argument": ("boys_q(x[i] + x[j], k, 0, f)) { err |= 1; break; }",
+                          "boys_q(x[i] + x[i], k, 0, f)) { err |= 1; break; }"),
+    "pairwise_sign": ("q_split(z, &z_hi[i], &z_lo[i]);", "q_split(-z, &z_hi[i], &z_lo[i]);"),
+    "pairwise_rows_scale": ("q_split(z, &z_hi[r], &z_lo[r]);", "q_split(z + z, &z_hi[r], &z_lo[r]);"),
 }
 
 

@@ -1,0 +1,66 @@
+"""The paper's benchmark workload (Section III, Algorithm 2) against the
+binary128 oracle.
+
+Tolerance: each F_l carries at most 5e-14, so |dz_i| <= 5e-14 sum_l|c_l|
+sum_j|y_j|, plus the FP64 rounding of the two sums (k+1 and n terms of size
+at most |c_l| |y_j|): 2^-53 (n + k + 2) sum_l|c_l| sum_j|y_j|.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_2512_10059_gb300 as pb
+from paper_2512_10059_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+
+
+def _tol(y, c, n, k):
+    s = np.abs(c).sum() * np.abs(y).sum()
+    return 5e-14 * s + 2.0 ** -53 * (n + k + 2) * s + 1e-27
+
+
+def _run(x, y, c):
+    z = pb.boys_pairwise(torch.from_numpy(x).to(DEV), torch.from_numpy(y).to(DEV), torch.from_numpy(c).to(DEV))
+    torch.cuda.synchronize()
+    return z.cpu().numpy()
+
+
+@pytest.mark.parametrize("n,k,sort", [(1, 0, True), (97, 5, False), (300, 12, True), (300, 12, False),
+                                      (257, 32, True), (200, 3, False)])
+def test_pairwise_vs_oracle(n, k, sort):
+    x, y, c = W.pairwise_alg2(n, k, seed=n + k, sort=sort)
+    got = _run(x, y, c)
+    hi, lo = oracle.pairwise(x, y, c)
+    err = np.abs((got - hi) - lo)
+    assert err.max() <= _tol(y, c, n, k), err.max()
+
+
+def test_pairwise_special_arguments():
+    x = np.array([0.0, 5.0, W.X0_PRINTED / 2, W.X1_PRINTED / 2, 15.0, 30.0])
+    y = np.array([1.0, -2.0, 0.5, 3.0, -1.0, 0.25])
+    c = np.array([1.0, -1.0, 0.5, 2.0])
+    got = _run(x, y, c)
+    hi, lo = oracle.pairwise(x, y, c)
+    assert np.max(np.abs((got - hi) - lo)) <= _tol(y, c, 6, 3)
+
+
+def test_pairwise_order_invariant():
+    x, y, c = W.pairwise_alg2(1000, 12, seed=5, sort=False)
+    perm = np.argsort(x)
+    z1 = _run(x, y, c)
+    z2 = _run(x[perm], y[perm], c)
+    assert np.max(np.abs(z1[perm] - z2)) <= _tol(y, c, 1000, 12)
+
+
+def test_pairwise_bench_size_sampled():
+    """N = 2^17 (the size bench.py times), sorted x on [0, 30], k = 12: eight
+    rows against the oracle."""
+    x, y, c = W.pairwise_alg2(1 << 17, 12, seed=8, sort=True)
+    got = _run(x, y, c)
+    rows = np.random.default_rng(0).choice(x.size, 8, replace=False)
+    hi, lo = oracle.pairwise_rows(x, y, c, rows)
+    err = np.abs((got[rows] - hi) - lo)
+    assert err.max() <= _tol(y, c, x.size, 12), err.max()
