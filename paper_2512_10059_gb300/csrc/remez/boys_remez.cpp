@@ -17,7 +17,9 @@
 //
 // The Remez iteration follows the six steps of Section II.B:
 //   1. initial equioscillation nodes (Chebyshev-distributed; randomly
-//      perturbed restarts if no pole-free solution exists),
+//      perturbed restarts if no pole-free solution exists; for strongly
+//      weighted problems, continuation from the unweighted problem through
+//      rho^s, s = 0, 1/4, ..., 1),
 //   2. solve rho (f - p/q)(x_i) = (-1)^i E at fixed nodes: functionals built
 //      from the nodes' divided-difference weights annihilate p, and a basis
 //      orthonormal in the weighted discrete inner product sum |w_i|/rho_i g h
@@ -226,7 +228,10 @@ struct Solver {
     const Problem& P;
     int n, m, N;
     real ta;  // a / b
+    real wexp = 1.0L;  // the weight used is rho^wexp (continuation from 0 to 1)
     std::vector<real> grid;
+
+    real rho(real x) const { return wexp == 1.0L ? P.rho(x) : powl(P.rho(x), wexp); }
 
     Solver(const Problem& pr, int n_, int m_) : P(pr), n(n_), m(m_), N(n_ + m_ + 2) {
         ta = P.a / P.b;
@@ -239,7 +244,7 @@ struct Solver {
 
     real err(const vec& p, const vec& q, real t) const {
         real x = t * P.b;
-        return P.rho(x) * (P.f(x) - peval(p, t) / peval(q, t));
+        return rho(x) * (P.f(x) - peval(p, t) / peval(q, t));
     }
 
     // Step 2 + 3: solve at nodes t, return false if no pole-free solution.
@@ -248,7 +253,7 @@ struct Solver {
         for (int i = 0; i < N; ++i) {
             real x = t[i] * P.b;
             f[i] = P.f(x);
-            rh[i] = P.rho(x);
+            rh[i] = rho(x);
             real prod = 1.0L;
             for (int j = 0; j < N; ++j)
                 if (j != i) prod *= (t[i] - t[j]);
@@ -362,82 +367,136 @@ struct Solver {
         return 0.5L * (lo + hi);
     }
 
-    Fit run(real target, unsigned seed) {
-        Fit out;
-        out.n = n;
-        out.m = m;
-        vec t(N);
-        unsigned long long rng = 0x9E3779B97F4A7C15ULL ^ seed;  // local xorshift: deterministic restarts
+    // Remez iterations from the nodes t.  Returns 1 on convergence (fit in
+    // out), 0 when the iteration breaks down (no pole-free solution, too few
+    // alternating extrema), -1 when Step 6 proves the target unreachable.
+    int iterate(vec& t, real target, Fit& out) const {
+        vec p, q;
+        real E = 0;
+        for (int iter = 0; iter < 80; ++iter) {
+            if (!solve(t, p, q, E)) return 0;  // Step 3 failed
+            // Step 4: error on the grid
+            std::vector<real> e(grid.size());
+            real mx = 0.0L;
+            for (size_t i = 0; i < grid.size(); ++i) {
+                e[i] = err(p, q, grid[i]);
+                mx = std::max(mx, fabsl(e[i]));
+            }
+            if (mx - fabsl(E) <= 2e-4L * fabsl(E)) {
+                out.ok = true;
+                out.E = fabsl(E);
+                out.maxerr = mx;
+                out.p = p;
+                out.q = q;
+                return 1;
+            }
+            // Step 5: local extrema of e on the grid (end points included),
+            // refined by golden section, grouped by sign.
+            std::vector<real> ext;
+            for (size_t i = 0; i < grid.size(); ++i) {
+                bool left = (i == 0) || fabsl(e[i]) >= fabsl(e[i - 1]);
+                bool right = (i + 1 == grid.size()) || fabsl(e[i]) >= fabsl(e[i + 1]);
+                if (!(left && right) || e[i] == 0) continue;
+                real x = grid[i];
+                if (i > 0 && i + 1 < grid.size())
+                    x = golden_max(p, q, grid[i - 1], grid[i + 1], e[i] > 0 ? 1 : -1);
+                ext.push_back(x);
+            }
+            // alternating subsequence: within runs of equal sign keep the largest
+            std::vector<real> alt;
+            std::vector<real> av;
+            for (real x : ext) {
+                real v = err(p, q, x);
+                if (!alt.empty() && ((v > 0) == (av.back() > 0))) {
+                    if (fabsl(v) > fabsl(av.back())) { alt.back() = x; av.back() = v; }
+                } else {
+                    alt.push_back(x);
+                    av.push_back(v);
+                }
+            }
+            if ((int)alt.size() < N) return 0;
+            // trim to N keeping the global maximum: drop the smaller end
+            while ((int)alt.size() > N) {
+                if (fabsl(av.front()) < fabsl(av.back())) { alt.erase(alt.begin()); av.erase(av.begin()); }
+                else { alt.pop_back(); av.pop_back(); }
+            }
+            // Step 6: de la Vallee-Poussin bound (only meaningful with the full weight)
+            real mn = 1e300L;
+            for (real v : av) mn = std::min(mn, fabsl(v));
+            if (wexp == 1.0L && mn > target) { out.ok = false; out.E = mn; return -1; }
+            t = alt;
+        }
+        return 0;
+    }
+
+    void initial_nodes(vec& t, int attempt, unsigned long long& rng) const {
         auto urand = [&rng]() {
             rng ^= rng << 13;
             rng ^= rng >> 7;
             rng ^= rng << 17;
             return (real)(rng >> 11) * (1.0L / 9007199254740992.0L);
         };
-        for (int attempt = 0; attempt < 6; ++attempt) {
-            for (int i = 0; i < N; ++i) {
-                real c = 0.5L * (1.0L - cosl(PI_L * i / (N - 1)));
-                if (attempt > 0 && i > 0 && i < N - 1) c += (urand() - 0.5L) * 0.4L / N;
-                t[i] = ta + (1.0L - ta) * c;
-            }
-            std::sort(t.begin(), t.end());
-            vec p, q;
-            real E = 0;
-            bool alive = true;
-            for (int iter = 0; iter < 80 && alive; ++iter) {
-                if (!solve(t, p, q, E)) { alive = false; break; }  // Step 3 failed: restart
-                // Step 4: error on the grid
-                std::vector<real> e(grid.size());
-                real mx = 0.0L;
-                for (size_t i = 0; i < grid.size(); ++i) {
-                    e[i] = err(p, q, grid[i]);
-                    mx = std::max(mx, fabsl(e[i]));
-                }
-                if (mx - fabsl(E) <= 2e-4L * fabsl(E)) {
-                    out.ok = true;
-                    out.E = fabsl(E);
-                    out.maxerr = mx;
-                    out.p = p;
-                    out.q = q;
-                    return out;
-                }
-                // Step 5: local extrema of e on the grid (end points included),
-                // refined by golden section, grouped by sign.
-                std::vector<real> ext;
-                for (size_t i = 0; i < grid.size(); ++i) {
-                    bool left = (i == 0) || fabsl(e[i]) >= fabsl(e[i - 1]);
-                    bool right = (i + 1 == grid.size()) || fabsl(e[i]) >= fabsl(e[i + 1]);
-                    if (!(left && right) || e[i] == 0) continue;
-                    real x = grid[i];
-                    if (i > 0 && i + 1 < grid.size())
-                        x = golden_max(p, q, grid[i - 1], grid[i + 1], e[i] > 0 ? 1 : -1);
-                    ext.push_back(x);
-                }
-                // alternating subsequence: within runs of equal sign keep the largest
-                std::vector<real> alt;
-                std::vector<real> av;
-                for (real x : ext) {
-                    real v = err(p, q, x);
-                    if (!alt.empty() && ((v > 0) == (av.back() > 0))) {
-                        if (fabsl(v) > fabsl(av.back())) { alt.back() = x; av.back() = v; }
-                    } else {
-                        alt.push_back(x);
-                        av.push_back(v);
-                    }
-                }
-                if ((int)alt.size() < N) { alive = false; break; }
-                // trim to N keeping the global maximum: drop the smaller end
-                while ((int)alt.size() > N) {
-                    if (fabsl(av.front()) < fabsl(av.back())) { alt.erase(alt.begin()); av.erase(av.begin()); }
-                    else { alt.pop_back(); av.pop_back(); }
-                }
-                // Step 6: de la Vallee-Poussin bound
-                real mn = 1e300L;
-                for (real v : av) mn = std::min(mn, fabsl(v));
-                if (mn > target) { out.ok = false; out.E = mn; return out; }
-                t = alt;
-            }
+        for (int i = 0; i < N; ++i) {
+            real c = 0.5L * (1.0L - cosl(PI_L * i / (N - 1)));
+            if (attempt > 0 && i > 0 && i < N - 1) c += (urand() - 0.5L) * 0.4L / N;
+            t[i] = ta + (1.0L - ta) * c;
         }
+        std::sort(t.begin(), t.end());
+    }
+
+    Fit run(real target, unsigned seed) {
+        Fit out;
+        out.n = n;
+        out.m = m;
+        vec t(N);
+        unsigned long long rng = 0x9E3779B97F4A7C15ULL ^ seed;  // local xorshift: deterministic restarts
+        // Step 1 with restarts (perturbed Chebyshev nodes)
+        for (int attempt = 0; attempt < 6; ++attempt) {
+            initial_nodes(t, attempt, rng);
+            wexp = 1.0L;
+            const int r = iterate(t, target, out);
+            if (r != 0) return out;
+        }
+        // Continuation in the weight for strongly weighted problems: solve
+        // with rho^s, s = 0, 1/4, ..., 1, each stage starting from the
+        // previous stage's equioscillation nodes.
+        initial_nodes(t, 0, rng);
+        for (int stage = 0; stage <= 4; ++stage) {
+            wexp = stage / 4.0L;
+            Fit tmp;
+            tmp.n = n;
+            tmp.m = m;
+            const int r = iterate(t, target, tmp);
+            if (r != 1) {
+                wexp = 1.0L;
+                out.ok = false;
+                if (r == -1) out.E = tmp.E;
+                return out;
+            }
+            if (stage == 4) { wexp = 1.0L; return tmp; }
+            // the converged nodes of this stage: alternating maxima of its error
+            vec nodes;
+            std::vector<real> vals;
+            for (size_t i = 0; i < grid.size(); ++i) {
+                const real v = err(tmp.p, tmp.q, grid[i]);
+                bool left = (i == 0) || fabsl(v) >= fabsl(err(tmp.p, tmp.q, grid[i - 1]));
+                bool right = (i + 1 == grid.size()) || fabsl(v) >= fabsl(err(tmp.p, tmp.q, grid[i + 1]));
+                if (!(left && right) || v == 0) continue;
+                if (!nodes.empty() && ((v > 0) == (vals.back() > 0))) {
+                    if (fabsl(v) > fabsl(vals.back())) { nodes.back() = grid[i]; vals.back() = v; }
+                } else {
+                    nodes.push_back(grid[i]);
+                    vals.push_back(v);
+                }
+            }
+            while ((int)nodes.size() > N) {
+                if (fabsl(vals.front()) < fabsl(vals.back())) { nodes.erase(nodes.begin()); vals.erase(vals.begin()); }
+                else { nodes.pop_back(); vals.pop_back(); }
+            }
+            if ((int)nodes.size() < N) { wexp = 1.0L; return out; }
+            t = nodes;
+        }
+        wexp = 1.0L;
         return out;
     }
 };
@@ -547,7 +606,98 @@ static void emit_vec(FILE* o, const std::vector<float>& v, int len) {
     fprintf(o, " }");
 }
 
+// ------------------------------------------------------------- FP64 tables (report)
+//
+// `boys_remez --fp64 KFIRST KLAST [--with-b]` regenerates the paper's FP64 table
+// set for eps_tol = 5e-14 (Appendix D): x0 by Eq. x0 for kmax = 32, x1 by Eq. x1,
+// r_{A,k} on [0, x0) with weight rho_{A,k} for k in [KFIRST, KLAST], and (with
+// --with-b) r_B on [x0, x1).  For each fit it prints the chosen (n, m) and the
+// levelled error, and checks Algorithm 1 evaluated in double precision with the
+// fitted anchor (rounded to double): the downward recurrence from r_{A,k} over
+// [0, x0) for every order 0..k, or the upward one from r_B over [x0, x1) for
+// orders 0..32.  The product's FP64 tables stay the printed ones; this is a
+// check of the generator against the paper's published result.
+
+static double horner_d(const std::vector<double>& c, double x) {
+    double v = c.back();
+    for (int i = (int)c.size() - 2; i >= 0; --i) v = fma(v, x, c[i]);
+    return v;
+}
+
+static real check_A_fp64(int k, const std::vector<double>& p, const std::vector<double>& q, double x0) {
+    real worst = 0.0L;
+    for (int i = 0; i < 6000; ++i) {
+        const double x = x0 * (i + 0.5) / 6000.0;
+        double F = horner_d(p, x) / horner_d(q, x);
+        const double e = exp(-x);
+        worst = std::max(worst, fabsl((real)F - boys_ref(k, x)));
+        for (int l = k - 1; l >= 0; --l) {
+            F = fma(2.0 * x, F, e) / (double)(2 * l + 1);
+            worst = std::max(worst, fabsl((real)F - boys_ref(l, x)));
+        }
+    }
+    return worst;
+}
+
+static real check_B_fp64(const std::vector<double>& p, const std::vector<double>& q, double x0, double x1) {
+    real worst = 0.0L;
+    for (int i = 0; i < 6000; ++i) {
+        const double x = x0 + (x1 - x0) * (i + 0.5) / 6000.0;
+        double F = horner_d(p, x) / horner_d(q, x);
+        const double e = exp(-x);
+        worst = std::max(worst, fabsl((real)F - boys_ref(0, x)));
+        for (int l = 0; l < 32; ++l) {
+            F = ((double)(2 * l + 1) * F - e) / (2.0 * x);
+            worst = std::max(worst, fabsl((real)F - boys_ref(l + 1, x)));
+        }
+    }
+    return worst;
+}
+
+static int run_fp64(int kfirst, int klast, bool with_b) {
+    const real eps = 5e-14L;
+    const real x0 = x0_of(32), x1 = x1_of(32, eps);
+    printf("x0 %.17Lg\nx1 %.17Lg\n", x0, x1);
+    const int nfit = klast - kfirst + 1 + (with_b ? 1 : 0);
+    int bad = 0;
+#pragma omp parallel for schedule(dynamic, 1) reduction(+ : bad)
+    for (int t = 0; t < nfit; ++t) {
+        const bool isB = with_b && t == nfit - 1;
+        Problem P = isB ? Problem{0, false, 32, x0, x1} : Problem{kfirst + t, true, kfirst + t, 0.0L, x0};
+        const Fit f = walsh_search(P, eps, 22);
+        if (!f.ok) {
+#pragma omp critical
+            {
+                printf("%s %d FAILED\n", isB ? "B" : "A", isB ? 0 : kfirst + t);
+                fflush(stdout);
+            }
+            ++bad;
+            continue;
+        }
+        const real b = isB ? x1 : x0;
+        vec px = to_x(f.p, b), qx = to_x(f.q, b);
+        const real lead = qx.back();
+        std::vector<double> pd, qd;
+        for (real v : px) pd.push_back((double)(v / lead));
+        for (real v : qx) qd.push_back((double)(v / lead));
+        const real err = isB ? check_B_fp64(pd, qd, (double)x0, (double)x1)
+                             : check_A_fp64(kfirst + t, pd, qd, (double)x0);
+#pragma omp critical
+        {
+            printf("%s %d n %d m %d E %.4Le fp64_alg1_max_err %.4Le\n", isB ? "B" : "A", isB ? 0 : kfirst + t,
+                   f.n, f.m, f.E, err);
+            fflush(stdout);
+        }
+    }
+    return bad ? 1 : 0;
+}
+
 int main(int argc, char** argv) {
+    if (argc > 1 && strcmp(argv[1], "--fp64") == 0) {
+        const int kf = argc > 2 ? atoi(argv[2]) : 0, kl = argc > 3 ? atoi(argv[3]) : 32;
+        const bool wb = argc > 4 && strcmp(argv[4], "--with-b") == 0;
+        return run_fp64(kf, kl, wb);
+    }
     const real eps_total = 1e-6L;   // FP32-tier tolerance (absolute)
     real eps_fit = 3e-7L;           // minimax target for the rational anchors
     const real eps_c = 3e-7L;       // region-C asymptotic budget (Eq. x1)
