@@ -77,6 +77,7 @@ struct Setup {
     bool valid, inA;
     double y0d, two_x, sd, inv2x;   // FP64 anchor, 2x, s = +-e^{-x} (0 in C), 1/(2x)
     xf::Xf y0, X2, Ev, R;           // the same in the 64-bit-significand format
+    xf::XfS Es;                     // s = +e^{-x} (A) or -e^{-x} (B), 0 (C), ready to add
 };
 
 template <int KMAX>
@@ -121,6 +122,7 @@ __device__ __forceinline__ Setup setup(double x) {
     S.X2 = xf::from_double(x);
     S.X2.e += 1;                                     // 2x, exact
     S.Ev = xf::from_double(inC ? 0.0 : e);           // zero in region C
+    S.Es = xf::prepare_addend(S.Ev, !inA);
     S.R = xf::from_double(inv2x);
     return S;
 }
@@ -171,6 +173,7 @@ __device__ __forceinline__ Setup setup_region(double x) {
     S.X2 = xf::from_double(x);
     S.X2.e += 1;
     S.R = xf::from_double(S.inv2x);
+    S.Es = xf::prepare_addend(S.Ev, R != kRegionA);
     return S;
 }
 
@@ -196,7 +199,7 @@ __device__ __forceinline__ xf::Xf step(const Setup& S, int j, xf::Xf y) {
     const int l = KMAX - 1 - j;
     const xf::Xf a = xf::select(S.inA, S.X2, xf::odd(j));
     const xf::Xf c = xf::select(S.inA, xf::recip_odd(l), S.R);
-    return xf::mul(xf::add_signed(xf::mul(a, y), S.Ev, !S.inA), c);
+    return xf::mul(xf::add_prepared(xf::mul_raw(a, y), S.Es), c);
 }
 
 __device__ __forceinline__ double out_value(const Setup& S, xf::Xf y) {

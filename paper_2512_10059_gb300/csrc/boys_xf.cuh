@@ -10,7 +10,9 @@
 // round-off analysis) is kept; results go back to IEEE doubles by integer
 // assembly of their bit patterns (truncation, < 1 ulp).  Products keep the
 // high 64 bits of the 128-bit significand product; sums align to the larger
-// exponent with 2 bits of headroom and renormalise with a leading-zero count.
+// exponent with 2 bits of headroom and renormalise with a leading-zero count
+// (the product feeding an addition skips its own renormalisation, and the
+// addend e^{-x} is shifted and signed once per argument).
 #pragma once
 
 #include <cstdint>
@@ -61,15 +63,34 @@ __device__ __forceinline__ Xf mul(Xf a, Xf b) {
     return r;
 }
 
-// t + s or t - s (sub = true) for t, s >= 0 whose exact result is >= 0; a
-// result at or below zero (cancellation beyond the precision) gives zero.
-__device__ __forceinline__ Xf add_signed(Xf t, Xf s, bool sub) {
+// Product without renormalisation: the high half of the significand product
+// with the exponent that keeps value = m * 2^(e - 63) exact (m then has up to
+// three leading zero bits).  For operands of an addition, which renormalises.
+__device__ __forceinline__ Xf mul_raw(Xf a, Xf b) {
+    Xf r;
+    r.m = __umul64hi(a.m, b.m);
+    r.e = a.e + b.e + 1;
+    return r;
+}
+
+// A signed addend prepared once: value = m * 2^(e - 61), |m| < 2^62.
+struct XfS {
+    long long m;
+    int e;
+};
+
+__device__ __forceinline__ XfS prepare_addend(Xf s, bool negate) {
+    const long long v = (long long)(s.m >> 2);
+    return XfS{negate ? -v : v, s.e};
+}
+
+// t + s for t >= 0 (normalised or not) and a prepared signed addend s whose
+// exact sum with t is >= 0; a result at or below zero gives zero.
+__device__ __forceinline__ Xf add_prepared(Xf t, XfS s) {
     const int E = max(t.e, s.e);
-    const int dt = min(E - t.e + 2, 63), ds = min(E - s.e + 2, 63);
-    const long long tm = (long long)(t.m >> dt);
-    long long sm = (long long)(s.m >> ds);
-    sm = sub ? -sm : sm;
-    const long long u = tm + sm;  // |tm|, |sm| < 2^62: no overflow
+    const long long tm = (long long)(t.m >> min(E - t.e + 2, 63));
+    const long long sm = s.m >> min(E - s.e, 63);  // arithmetic shift keeps the sign
+    const long long u = tm + sm;                   // |tm|, |sm| < 2^62: no overflow
     const int lz = __clzll(u);
     Xf r;
     r.m = (unsigned long long)u << lz;
