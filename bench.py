@@ -51,7 +51,10 @@ HBM_FALLBACK_GBS = 6800.0
 # DRAM bytes per argument of the timed kernel from one ncu capture at N = 2^22
 # (profiles/k_eval_f64_kmax32_eri_mixture.md), scaled to the launch by the
 # arguments it processes; None whenever the kernel changed since that capture.
-TRAFFIC_BYTES_PER_X = 259.2
+TRAFFIC_BYTES_PER_X = 267.3
+
+
+ALL_MODES = ("fused", "fp32", "grad", "pairwise", "ragged")
 
 
 def peaks():
@@ -197,6 +200,7 @@ def run_reference(args):
 
 def run_ours(args):
     import torch
+    modes = args.modes
     ws, rank, local = dist_env()
     dist = None
     if ws > 1:
@@ -279,9 +283,23 @@ def run_ours(args):
     roof["hbm_frac"] = bytes_per_launch / avg_launch_s / 1e9 / hbm_gbs
     roof["fp64_frac"] = flops_per_launch / avg_launch_s / 1e12 / FP64_PEAK_TFLOPS
 
+    def time_launches(fn, reps):
+        """Mean device time of one launch of fn on the stream, after warm-up."""
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize(dev)
+        a0 = torch.cuda.Event(enable_timing=True)
+        a1 = torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        for _ in range(reps):
+            fn()
+        a1.record(stream)
+        torch.cuda.synchronize(dev)
+        return a0.elapsed_time(a1) / reps
+
     # fused consumer on the same arguments (one extra input rho, one output per x)
     fused = None
-    if not args.skip_modes:
+    if "fused" in modes:
         rho = torch.from_numpy(W.rho_c2(n, seed=2)).to(dev)
         fout = torch.empty(n, dtype=torch.float64, device=dev)
         for _ in range(args.warmup):
@@ -305,20 +323,7 @@ def run_ours(args):
     # FP32 tier on the same arguments (rounded to float) and on the FP32-tier
     # workload (parity mixture, N = 2^26) at kmax 4 / 12 / 24 next to FP64
     fp32 = None
-    if not args.skip_modes:
-        def time_launches(fn, reps):
-            for _ in range(args.warmup):
-                fn()
-            torch.cuda.synchronize(dev)
-            a0 = torch.cuda.Event(enable_timing=True)
-            a1 = torch.cuda.Event(enable_timing=True)
-            a0.record(stream)
-            for _ in range(reps):
-                fn()
-            a1.record(stream)
-            torch.cuda.synchronize(dev)
-            return a0.elapsed_time(a1) / reps
-
+    if "fp32" in modes:
         reps = max(5, min(args.steps, 20))
         xf = x.float()
         of = torch.empty((KMAX + 1, n), dtype=torch.float32, device=dev)
@@ -346,7 +351,7 @@ def run_ours(args):
     # backward: N = 2^24 (2^(n_log2 - 2) when profiling), kmax = 16, x log-uniform
     # [1e-10, 1e3], upstream gradients N(0,1) drawn on the device (seeded)
     grad = None
-    if not args.skip_modes:
+    if "grad" in modes:
         ng = n >> 2
         kg = 16
         xg = torch.from_numpy(W.log_uniform(W.uniform01(W.stream_key(5, 1), ng), 1e-10, 1e3)).to(dev)
@@ -364,7 +369,7 @@ def run_ours(args):
     # paper's N = 2^19 by the n^2 law.  The paper's own figure (72 s on an
     # NVIDIA A100) is context, not a target.
     pair = None
-    if not args.skip_modes:
+    if "pairwise" in modes:
         npw = 1 << max(10, args.n_log2 - 9)
         xs, ys, cs = W.pairwise_alg2(npw, 12, seed=8, sort=True)
         xpt, ypt, cpt = (torch.from_numpy(a).to(dev) for a in (xs, ys, cs))
@@ -381,7 +386,7 @@ def run_ours(args):
         del xpt, ypt, cpt, zpt, xut, yut
 
     ragged = None
-    if not args.skip_modes:
+    if "ragged" in modes:
         x3, off3, km3 = W.ragged_c3()
         xt3 = torch.from_numpy(x3).to(dev)
         ot3 = torch.from_numpy(off3).to(dev)
@@ -460,7 +465,8 @@ def run_ours(args):
                        "region_fractions_ABC": [round(f, 4) for f in fracs],
                        "l2": "inputs larger than L2 (x 0.54 GB read, 17.7 GB written per step); no flush",
                        "parallelism": f"replicas x{ws}, no data-path collective"},
-            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": args.steps,
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": args.steps,
             "clocks": clocks, "modes": {"fused_kmax32": fused, "ragged_4096seg": ragged, "fp32_tier": fp32, "grad_kmax16": grad,
                       "pairwise_alg2_k12": pair},
         }
@@ -483,8 +489,13 @@ def main():
                     help="arguments per GPU = 2^n (26 is the benchmarked workload; smaller only for profiling)")
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
-    ap.add_argument("--skip-modes", action="store_true")
+    ap.add_argument("--modes", default=",".join(ALL_MODES),
+                    help="comma list of the secondary modes to time (" + ",".join(ALL_MODES) + "), or none")
+    ap.add_argument("--skip-modes", action="store_true", help="same as --modes none")
     args = ap.parse_args()
+    args.modes = set() if args.skip_modes or args.modes == "none" else set(args.modes.split(","))
+    if args.modes - set(ALL_MODES):
+        ap.error(f"unknown modes {sorted(args.modes - set(ALL_MODES))}")
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":

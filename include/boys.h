@@ -70,8 +70,7 @@ boys_status boys_diag_math(int fn, const double* a, const double* b, int64_t n, 
 
 /*
  * FP64 stored mode — Algorithm 1 for every x_i.
- *   x    [n]            input arguments (8-byte aligned; 16-byte alignment
- *                       of x, out and an even ld enable 128-bit accesses)
+ *   x    [n]            input arguments (8-byte aligned)
  *   n                   number of arguments, n >= 0
  *   kmax                highest order, 0 <= kmax <= 32
  *   out  [kmax+1][ld]   F_k(x_i) at out[k*ld + i]; ld >= n

@@ -13,7 +13,15 @@
 
 // Minimum resident blocks per SM for the stored-mode kernel (caps registers).
 #ifndef BOYS_STORED_MIN_BLOCKS
-#define BOYS_STORED_MIN_BLOCKS 8
+#define BOYS_STORED_MIN_BLOCKS 10
+#endif
+// FP64 recurrence steps and minimum resident blocks of the fused kernel, whose
+// Horner sum adds KMAX FMAs per argument to the FP64 pipe.
+#ifndef BOYS_FUSED_FP64_STEPS
+#define BOYS_FUSED_FP64_STEPS 2
+#endif
+#ifndef BOYS_FUSED_MIN_BLOCKS
+#define BOYS_FUSED_MIN_BLOCKS 8
 #endif
 
 namespace boys {
@@ -31,13 +39,13 @@ __global__ void __launch_bounds__(kBlock, BOYS_STORED_MIN_BLOCKS) k_eval_f64(con
 
 // out[i] = sum_k (-2 rho_i)^k F_k(x_i), by Horner in a = -2 rho from F_KMAX down.
 template <int KMAX>
-__global__ void __launch_bounds__(kBlock) k_fused_f64(const double* __restrict__ x,
+__global__ void __launch_bounds__(kBlock, BOYS_FUSED_MIN_BLOCKS) k_fused_f64(const double* __restrict__ x,
                                                       const double* __restrict__ rho, int64_t n,
                                                       double* __restrict__ out) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
         double F[KMAX + 1];
-        fp64::eval_point<KMAX>(__ldcs(x + i), F);
+        fp64::eval_point<KMAX, BOYS_FUSED_FP64_STEPS>(__ldcs(x + i), F);
         const double a = -2.0 * __ldcs(rho + i);
         double s = F[KMAX];
 #pragma unroll

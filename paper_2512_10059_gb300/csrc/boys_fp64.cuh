@@ -36,9 +36,10 @@ namespace fp64 {
 // Recurrence steps that run in FP64; the rest use the 64-bit-significand
 // integer format (boys_xf.cuh).  Splitting the steps balances the FP64 pipe
 // (anchors, e^{-x}, reciprocals and these steps) against the integer pipes;
-// 8 was fastest in a sweep over 0..12 on GB300 (kmax = 32 stored mode).
+// 7 was fastest in a sweep over 3..8 on GB300 (kmax = 32 stored mode, with the
+// 48-register cap of 10 resident blocks per SM).
 #ifndef BOYS_FP64_STEPS
-#define BOYS_FP64_STEPS 8
+#define BOYS_FP64_STEPS 7
 #endif
 
 constexpr int kRaN[33] = BOYS_RA_N_INIT;
@@ -80,18 +81,37 @@ struct Setup {
     xf::XfS Es;                     // s = +e^{-x} (A) or -e^{-x} (B), 0 (C), ready to add
 };
 
-template <int KMAX>
-__device__ __forceinline__ Setup setup(double x) {
+enum Region { kRegionA = 0, kRegionB = 1, kRegionC = 2, kRegionNone = 3 };
+
+// Set-up for one argument.  MODE = kRegionNone takes any x (branch-free:
+// every lane evaluates the arithmetic of all three regions and selects);
+// MODE = kRegionA/B/C is for x known to be valid and in that region, where
+// the other regions' work folds away at compile time.
+//
+// Branch-free, one inverse square root serves all three anchors (one Newton
+// iteration pair instead of three): r = z^{-1/2} with z = q^2 in A, (2x q)^2
+// in B and x in C, so that
+//   A: p/q = sign(q) p r,  B: p/q = sign(q) 2x p r,  1/(2x) = |q| r,
+//   C: F_0 = (sqrt(pi)/2) r,  1/(2x) = r (r/2).
+// (q keeps one sign on each region's interval and |q| lies in [2e7, 7e16]
+// for every table row, so the squares stay normal.)  A single region takes
+// its cheapest form instead: the Newton quotient p/q in A and B, 1/(2x) by a
+// Newton reciprocal in B, and r (r/2) from the inverse square root in C.
+template <int MODE, int KMAX>
+__device__ __forceinline__ Setup setup_mode(double x) {
     static_assert(KMAX >= 0 && KMAX <= 32, "tables cover orders 0..32");
     constexpr int NP = Degrees<KMAX>::NP;
     constexpr int NQ = Degrees<KMAX>::NQ;
 
     long long xb = __double_as_longlong(x);
     if (xb == (long long)0x8000000000000000ULL) xb = 0;  // -0.0 -> +0.0
-    const bool valid = xb >= 0 && xb <= kBitsInf;         // x < 0 and NaN -> NaN everywhere
+    bool valid = true, inA = MODE == kRegionA, inC = MODE == kRegionC;
+    if (MODE == kRegionNone) {
+        valid = xb >= 0 && xb <= kBitsInf;                // x < 0 and NaN -> NaN everywhere
+        inA = valid && xb < kBitsX0;
+        inC = !valid || xb >= kBitsX1;
+    }
     x = valid ? __longlong_as_double(xb) : quiet_nan();
-    const bool inA = valid && xb < kBitsX0;
-    const bool inC = !valid || xb >= kBitsX1;
 
     // Anchor: r_{A,KMAX} in A, r_B in B (Horner, monic denominators).
     double p = inA ? c_ra_p[KMAX][NP] : c_rb_p[NP];
@@ -100,22 +120,38 @@ __device__ __forceinline__ Setup setup(double x) {
     double q = inA ? c_ra_q[KMAX][NQ] : c_rb_q[NQ];
 #pragma unroll
     for (int i = NQ - 1; i >= 0; --i) q = fma(q, x, inA ? c_ra_q[KMAX][i] : c_rb_q[i]);
-    const double rat = dmath::div(p, q);
 
-    // Region C anchor and the step factor 1/(2x) of B and C; arguments beyond
-    // 1e300 are clamped there (F_0 < 1e-150 and F_k = 0 for k > 0 either way),
-    // +inf gives exactly 0.
+    // Arguments beyond 1e300 are clamped there in C (F_0 < 1e-150 and F_k = 0
+    // for k > 0 either way); +inf gives exactly 0.
     const bool huge = xb > kBits1e300 && xb <= kBitsInf;
     const double xr = huge ? 1e300 : x;
-    const double asym0 = (xb == kBitsInf) ? 0.0 : kSqrtPiOver2 * dmath::rsqrt(xr);
-    const double inv2x = dmath::rcp(xr + xr);
+    const double two_x = x + x;
+    double rat, asym0, inv2x;
+    if (MODE == kRegionNone) {
+        const double t = inA ? q : two_x * q;
+        const double r = dmath::rsqrt(inC ? xr : t * t);
+        const double ps =
+            __longlong_as_double(__double_as_longlong(p) ^ (__double_as_longlong(t) & (long long)0x8000000000000000ULL));
+        rat = r * (inA ? ps : ps * two_x);
+        asym0 = (xb == kBitsInf) ? 0.0 : kSqrtPiOver2 * r;
+        inv2x = r * (inC ? 0.5 * r : fabs(q));
+    } else if (MODE == kRegionC) {
+        const double r = dmath::rsqrt(xr);
+        rat = 0.0;
+        asym0 = (xb == kBitsInf) ? 0.0 : kSqrtPiOver2 * r;
+        inv2x = r * (0.5 * r);
+    } else {
+        rat = dmath::div(p, q);
+        asym0 = 0.0;
+        inv2x = MODE == kRegionB ? dmath::rcp(two_x) : 0.0;
+    }
     const double e = dmath::exp_neg(inC ? 0.0 : x);
 
     Setup S;
     S.valid = valid;
     S.inA = inA;
     S.y0d = inC ? asym0 : rat;
-    S.two_x = x + x;
+    S.two_x = two_x;
     S.sd = inC ? 0.0 : (inA ? e : -e);
     S.inv2x = inv2x;
     S.y0 = xf::from_double(S.y0d);
@@ -127,10 +163,10 @@ __device__ __forceinline__ Setup setup(double x) {
     return S;
 }
 
-// Region-restricted set-up, for warps whose lanes all lie in one region R
-// (0 = A, 1 = B, 2 = C): only that region's anchor and special functions are
-// evaluated.  x must be valid (the caller classifies first).
-enum Region { kRegionA = 0, kRegionB = 1, kRegionC = 2, kRegionNone = 3 };
+template <int KMAX>
+__device__ __forceinline__ Setup setup(double x) {
+    return setup_mode<kRegionNone, KMAX>(x);
+}
 
 __device__ __forceinline__ int region_of(double x) {
     long long xb = __double_as_longlong(x);
@@ -139,53 +175,15 @@ __device__ __forceinline__ int region_of(double x) {
     return xb < kBitsX0 ? kRegionA : (xb < kBitsX1 ? kRegionB : kRegionC);
 }
 
-template <int R, int KMAX>
-__device__ __forceinline__ Setup setup_region(double x) {
-    Setup S;
-    S.valid = true;
-    S.inA = (R == kRegionA);
-    x = fabs(x);  // -0.0 -> +0.0 (x >= 0 here)
-    if (R == kRegionC) {
-        const long long xb = __double_as_longlong(x);
-        const bool huge = xb > kBits1e300;
-        const double xr = huge ? 1e300 : x;
-        S.y0d = (xb == kBitsInf) ? 0.0 : kSqrtPiOver2 * dmath::rsqrt(xr);
-        S.inv2x = dmath::rcp(xr + xr);
-        S.sd = 0.0;
-        S.Ev = xf::zero();
-    } else {
-        constexpr int N = R == kRegionA ? kRaN[KMAX] : BOYS_RB_N;
-        constexpr int M = R == kRegionA ? kRaM[KMAX] : BOYS_RB_M;
-        double p = R == kRegionA ? c_ra_p[KMAX][N] : c_rb_p[N];
-#pragma unroll
-        for (int i = N - 1; i >= 0; --i) p = fma(p, x, R == kRegionA ? c_ra_p[KMAX][i] : c_rb_p[i]);
-        double q = R == kRegionA ? c_ra_q[KMAX][M] : c_rb_q[M];
-#pragma unroll
-        for (int i = M - 1; i >= 0; --i) q = fma(q, x, R == kRegionA ? c_ra_q[KMAX][i] : c_rb_q[i]);
-        S.y0d = dmath::div(p, q);
-        const double e = dmath::exp_neg(x);
-        S.sd = R == kRegionA ? e : -e;
-        S.inv2x = R == kRegionB ? dmath::rcp(x + x) : 0.0;
-        S.Ev = xf::from_double(e);
-    }
-    S.two_x = x + x;
-    S.y0 = xf::from_double(S.y0d);
-    S.X2 = xf::from_double(x);
-    S.X2.e += 1;
-    S.R = xf::from_double(S.inv2x);
-    S.Es = xf::prepare_addend(S.Ev, R != kRegionA);
-    return S;
-}
-
 // Warp-level choice of set-up: the region-restricted one when every lane of
 // the warp is in the same region, the branch-free one otherwise.  All 32
 // lanes must call it together.
 template <int KMAX>
 __device__ __forceinline__ Setup setup_warp(double x) {
     const int r = region_of(x);
-    if (__all_sync(0xffffffffu, r == kRegionA)) return setup_region<kRegionA, KMAX>(x);
-    if (__all_sync(0xffffffffu, r == kRegionB)) return setup_region<kRegionB, KMAX>(x);
-    if (__all_sync(0xffffffffu, r == kRegionC)) return setup_region<kRegionC, KMAX>(x);
+    if (__all_sync(0xffffffffu, r == kRegionA)) return setup_mode<kRegionA, KMAX>(x);
+    if (__all_sync(0xffffffffu, r == kRegionB)) return setup_mode<kRegionB, KMAX>(x);
+    if (__all_sync(0xffffffffu, r == kRegionC)) return setup_mode<kRegionC, KMAX>(x);
     return setup<KMAX>(x);
 }
 
@@ -202,8 +200,11 @@ __device__ __forceinline__ xf::Xf step(const Setup& S, int j, xf::Xf y) {
     return xf::mul(xf::add_prepared(xf::mul_raw(a, y), S.Es), c);
 }
 
+// One select per output: NaN for an invalid argument, 0 below the normal
+// range (see xf::to_double), the value otherwise.
 __device__ __forceinline__ double out_value(const Setup& S, xf::Xf y) {
-    return S.valid ? xf::to_double(y) : quiet_nan();
+    const double flush = S.valid ? 0.0 : quiet_nan();
+    return (y.e < -1022 || !S.valid) ? flush : __longlong_as_double((long long)xf::double_bits(y));
 }
 
 // The same step in FP64 (y_{j+1} = fma(a_j, y_j, s) * c_j).

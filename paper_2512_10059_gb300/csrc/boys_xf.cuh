@@ -46,12 +46,18 @@ __device__ __forceinline__ Xf from_double(double d) {
     return be == 0 ? zero() : r;
 }
 
-// Xf -> double, truncating the significand to 53 bits; values below the
-// normal range flush to zero.
+// Bit pattern of a normalised Xf as a double, truncating the significand to
+// 53 bits; meaningful for -1022 <= e <= 1023.
+__device__ __forceinline__ unsigned long long double_bits(Xf v) {
+    return ((unsigned long long)(long long)(v.e + 1022) << 52) + (v.m >> 11);  // the hidden bit adds the last 1
+}
+
+// Xf -> double; values below the normal range flush to zero.  Every zero of
+// this format (from zero(), or a product or sum with a zero operand) carries
+// an exponent within a few thousand of kXfZeroExp, so the exponent test alone
+// also catches m == 0.
 __device__ __forceinline__ double to_double(Xf v) {
-    const unsigned long long bits =
-        ((unsigned long long)(long long)(v.e + 1022) << 52) + (v.m >> 11);  // the hidden bit adds the last 1
-    return (v.m == 0 || v.e < -1022) ? 0.0 : __longlong_as_double((long long)bits);
+    return v.e < -1022 ? 0.0 : __longlong_as_double((long long)double_bits(v));
 }
 
 __device__ __forceinline__ Xf mul(Xf a, Xf b) {

@@ -67,15 +67,15 @@ def test_sizes_and_ragged_tails(n):
 def test_unaligned_and_strided_layouts():
     x = W.mixture_c1(5001, seed=21)
     base = torch.from_numpy(np.concatenate([[0.0], x])).to(DEV)
-    xv = base[1:]                       # 8-byte but not 16-byte aligned: scalar path
+    xv = base[1:]                       # 8-byte but not 16-byte aligned
     buf = torch.full((9, 5003), -7.0, dtype=torch.float64, device=DEV)
-    out = buf[:, :5001]                 # ld = 5003 (odd): scalar stores
+    out = buf[:, :5001]                 # ld = 5003 (odd row stride)
     pb.boys_eval(xv, 8, out=out)
     ref_vec = pb.boys_eval(torch.from_numpy(x).to(DEV), 8)
     torch.cuda.synchronize()
     got = out.cpu().numpy()
     _check(x, got, 8, "unaligned")
-    assert np.array_equal(got, ref_vec.cpu().numpy()), "scalar and 128-bit paths differ bitwise"
+    assert np.array_equal(got, ref_vec.cpu().numpy()), "layout changed the bits"
     assert torch.all(buf[:, 5001:] == -7.0), "wrote outside [0, n) of a row"
 
 
