@@ -354,14 +354,18 @@ def run_ours(args):
     if "grad" in modes:
         ng = n >> 2
         kg = 16
-        xg = torch.from_numpy(W.log_uniform(W.uniform01(W.stream_key(5, 1), ng), 1e-10, 1e3)).to(dev)
+        xg_host = W.log_uniform(W.uniform01(W.stream_key(5, 1), ng), 1e-10, 1e3)
+        xg = torch.from_numpy(xg_host).to(dev)
         gen = torch.Generator(device=dev)
         gen.manual_seed(6)
         gg = torch.randn((kg + 1, ng), dtype=torch.float64, device=dev, generator=gen)
         dxg = torch.empty(ng, dtype=torch.float64, device=dev)
         gms = time_launches(lambda: pb.boys_grad(xg, gg, kg, out=dxg), max(5, min(args.steps, 20)))
+        # algorithmic work: the forward at order kmax + 1 plus kmax + 1 FMAs
+        gfl = ng * (flops_per_x(xg_host, kg + 1)[0] + 2 * (kg + 1))
         grad = {"value": ng * (kg + 1) / (gms / 1e3), "unit": "dL/dF_k terms/s", "ms": gms, "n": ng, "kmax": kg,
-                "hbm_gbs": ng * 8 * (kg + 3) / (gms / 1e3) / 1e9}
+                "hbm_gbs": ng * 8 * (kg + 3) / (gms / 1e3) / 1e9,
+                "fp64_frac": gfl / (gms / 1e3) / 1e12 / FP64_PEAK_TFLOPS}
         del xg, gg, dxg
 
     # the paper's benchmark workload (Section III, Algorithm 2): k = 12,
@@ -406,9 +410,11 @@ def run_ours(args):
         lens = np.diff(off3)
         nval = int(np.sum((km3.astype(np.int64) + 1) * lens))
         rbytes = 8 * x3.size + 8 * nval + 20 * km3.size
+        rfl = sum(flops_per_x(x3[off3[j]:off3[j + 1]], int(km3[j]))[0] * int(lens[j]) for j in range(km3.size))
         ragged = {"value": nval / (rms / 1e3), "unit": UNIT, "ms_per_step": rms, "arguments": int(x3.size),
                   "segments": int(km3.size), "mean_kmax_weighted": float(np.sum(km3 * lens) / lens.sum()),
-                  "hbm_gbs": rbytes / (rms / 1e3) / 1e9, "config": plan.config(),
+                  "hbm_gbs": rbytes / (rms / 1e3) / 1e9,
+                  "fp64_frac": rfl / (rms / 1e3) / 1e12 / FP64_PEAK_TFLOPS, "config": plan.config(),
                   "launch": "one cudaGraphLaunch (workspace memset + persistent kernel)"}
         plan.close()
         del xt3, ot3, kt3, plan

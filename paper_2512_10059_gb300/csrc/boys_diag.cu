@@ -1,8 +1,10 @@
-// Diagnostic entry point: evaluates the FP64 elementary functions of
-// boys_math.cuh elementwise, so that tests can measure them against CUDA's
-// own functions and an extended-precision reference.
+// Diagnostic entry point: evaluates the elementary functions of boys_math.cuh
+// (FP64) and boys_xf.cuh (integer pipes) elementwise, so that tests can
+// measure them against CUDA's own functions and an extended-precision
+// reference.
 #include "boys_internal.h"
 #include "boys_math.cuh"
+#include "boys_xf.cuh"
 
 namespace boys {
 namespace {
@@ -17,7 +19,13 @@ __global__ void k_diag_math(int fn, const double* __restrict__ a, const double* 
             case 0: r = dmath::exp_neg(v); break;
             case 1: r = dmath::rcp(v); break;
             case 2: r = dmath::div(b[i], v); break;
-            default: r = dmath::rsqrt(v); break;
+            case 3: r = dmath::rsqrt(v); break;
+            default: {  // integer-pipe e^{-v}, its 64-bit significand rounded to nearest
+                const xf::Xf e = xf::exp_neg(v);
+                const double hi = (double)(e.m >> 11), lo = (double)(e.m & 0x7FF);
+                r = ldexp(hi + lo * 0x1p-11, e.e - 52);
+                break;
+            }
         }
         out[i] = r;
     }
@@ -28,7 +36,7 @@ __global__ void k_diag_math(int fn, const double* __restrict__ a, const double* 
 
 BOYS_API boys_status boys_diag_math(int fn, const double* a, const double* b, int64_t n, double* out, void* stream) {
     using namespace boys;
-    if (fn < 0 || fn > 3) return fail(BOYS_ERR_INVALID_ARG, "boys_diag_math: fn=%d outside [0, 3]", fn);
+    if (fn < 0 || fn > 4) return fail(BOYS_ERR_INVALID_ARG, "boys_diag_math: fn=%d outside [0, 4]", fn);
     if (n < 0) return fail(BOYS_ERR_INVALID_ARG, "boys_diag_math: n < 0");
     if (n == 0) return BOYS_OK;
     if (!a || !out || (fn == 2 && !b)) return fail(BOYS_ERR_INVALID_ARG, "boys_diag_math: NULL pointer");

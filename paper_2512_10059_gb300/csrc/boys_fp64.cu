@@ -15,10 +15,15 @@
 #ifndef BOYS_STORED_MIN_BLOCKS
 #define BOYS_STORED_MIN_BLOCKS 10
 #endif
-// FP64 recurrence steps and minimum resident blocks of the fused kernel, whose
-// Horner sum adds KMAX FMAs per argument to the FP64 pipe.
+// FP64 recurrence steps and minimum resident blocks of the fused kernel.  Its
+// Horner sum adds KMAX FMAs per argument to the FP64 pipe, so every step runs
+// in the integer format (swept on GB300 at kmax 8..32 x 0..4 FP64 steps: 0
+// was fastest at every kmax).
 #ifndef BOYS_FUSED_FP64_STEPS
-#define BOYS_FUSED_FP64_STEPS 2
+#define BOYS_FUSED_FP64_STEPS 0
+#endif
+#ifndef BOYS_FUSED_INT_EXP
+#define BOYS_FUSED_INT_EXP 1
 #endif
 #ifndef BOYS_FUSED_MIN_BLOCKS
 #define BOYS_FUSED_MIN_BLOCKS 8
@@ -45,7 +50,7 @@ __global__ void __launch_bounds__(kBlock, BOYS_FUSED_MIN_BLOCKS) k_fused_f64(con
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
         double F[KMAX + 1];
-        fp64::eval_point<KMAX, BOYS_FUSED_FP64_STEPS>(__ldcs(x + i), F);
+        fp64::eval_point<KMAX, BOYS_FUSED_FP64_STEPS, (BOYS_FUSED_INT_EXP != 0) && BOYS_FUSED_FP64_STEPS == 0>(__ldcs(x + i), F);
         const double a = -2.0 * __ldcs(rho + i);
         double s = F[KMAX];
 #pragma unroll

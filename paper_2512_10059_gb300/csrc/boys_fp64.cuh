@@ -34,13 +34,30 @@ namespace boys {
 namespace fp64 {
 
 // Recurrence steps that run in FP64; the rest use the 64-bit-significand
-// integer format (boys_xf.cuh).  Splitting the steps balances the FP64 pipe
-// (anchors, e^{-x}, reciprocals and these steps) against the integer pipes;
-// 7 was fastest in a sweep over 3..8 on GB300 (kmax = 32 stored mode, with the
-// 48-register cap of 10 resident blocks per SM).
-#ifndef BOYS_FP64_STEPS
-#define BOYS_FP64_STEPS 7
+// integer format (boys_xf.cuh).  The set-up (anchors, e^{-x}, the inverse
+// square root) loads the FP64 pipe with the same work for every kmax, while
+// the integer pipes take one step per order: up to about 24 integer steps
+// hide behind the set-up, beyond that each further order is cheaper in FP64.
+// Swept on GB300 (stored mode, kmax 1..32 x 0..8 FP64 steps, 10 blocks per
+// SM): 0 for kmax <= 24, then kmax - 24 up to 28 and kmax - 25 after (7 at
+// kmax = 32).  Defining BOYS_FP64_STEPS forces one value for every kmax.
+// e^{-x} runs on the integer pipes (xf::exp_neg) when no step runs in FP64
+// and the integer pipes still have room: up to kmax = 22 (swept with the split
+// above; at 23 and 24 the integer steps alone nearly fill those pipes).
+#ifndef BOYS_INT_EXP_MAX_KMAX
+#define BOYS_INT_EXP_MAX_KMAX 22
 #endif
+constexpr bool int_exp_for(int kmax, int nsteps_fp64) {
+    return (nsteps_fp64 < kmax ? nsteps_fp64 : kmax) == 0 && kmax <= BOYS_INT_EXP_MAX_KMAX;
+}
+
+constexpr int fp64_steps_for(int kmax) {
+#ifdef BOYS_FP64_STEPS
+    return BOYS_FP64_STEPS + 0 * kmax;
+#else
+    return kmax <= 24 ? 0 : (kmax <= 28 ? kmax - 24 : kmax - 25);
+#endif
+}
 
 constexpr int kRaN[33] = BOYS_RA_N_INIT;
 constexpr int kRaM[33] = BOYS_RA_M_INIT;
@@ -97,7 +114,7 @@ enum Region { kRegionA = 0, kRegionB = 1, kRegionC = 2, kRegionNone = 3 };
 // for every table row, so the squares stay normal.)  A single region takes
 // its cheapest form instead: the Newton quotient p/q in A and B, 1/(2x) by a
 // Newton reciprocal in B, and r (r/2) from the inverse square root in C.
-template <int MODE, int KMAX>
+template <int MODE, int KMAX, bool INT_EXP = false>
 __device__ __forceinline__ Setup setup_mode(double x) {
     static_assert(KMAX >= 0 && KMAX <= 32, "tables cover orders 0..32");
     constexpr int NP = Degrees<KMAX>::NP;
@@ -145,7 +162,17 @@ __device__ __forceinline__ Setup setup_mode(double x) {
         asym0 = 0.0;
         inv2x = MODE == kRegionB ? dmath::rcp(two_x) : 0.0;
     }
-    const double e = dmath::exp_neg(inC ? 0.0 : x);
+    // e^{-x}: on the integer pipes, straight into the recurrence's format, when
+    // no step runs in FP64 (the FP64 copy is then only assembled if used)
+    double e;
+    xf::Xf E;
+    if (INT_EXP) {
+        E = xf::exp_neg(inC ? 0.0 : x);
+        e = xf::to_double(E);
+    } else {
+        e = dmath::exp_neg(inC ? 0.0 : x);
+        E = xf::from_double(e);
+    }
 
     Setup S;
     S.valid = valid;
@@ -157,15 +184,15 @@ __device__ __forceinline__ Setup setup_mode(double x) {
     S.y0 = xf::from_double(S.y0d);
     S.X2 = xf::from_double(x);
     S.X2.e += 1;                                     // 2x, exact
-    S.Ev = xf::from_double(inC ? 0.0 : e);           // zero in region C
+    S.Ev = inC ? xf::zero() : E;                     // zero in region C
     S.Es = xf::prepare_addend(S.Ev, !inA);
     S.R = xf::from_double(inv2x);
     return S;
 }
 
-template <int KMAX>
+template <int KMAX, bool INT_EXP = false>
 __device__ __forceinline__ Setup setup(double x) {
-    return setup_mode<kRegionNone, KMAX>(x);
+    return setup_mode<kRegionNone, KMAX, INT_EXP>(x);
 }
 
 __device__ __forceinline__ int region_of(double x) {
@@ -178,13 +205,13 @@ __device__ __forceinline__ int region_of(double x) {
 // Warp-level choice of set-up: the region-restricted one when every lane of
 // the warp is in the same region, the branch-free one otherwise.  All 32
 // lanes must call it together.
-template <int KMAX>
+template <int KMAX, bool INT_EXP = false>
 __device__ __forceinline__ Setup setup_warp(double x) {
     const int r = region_of(x);
-    if (__all_sync(0xffffffffu, r == kRegionA)) return setup_mode<kRegionA, KMAX>(x);
-    if (__all_sync(0xffffffffu, r == kRegionB)) return setup_mode<kRegionB, KMAX>(x);
-    if (__all_sync(0xffffffffu, r == kRegionC)) return setup_mode<kRegionC, KMAX>(x);
-    return setup<KMAX>(x);
+    if (__all_sync(0xffffffffu, r == kRegionA)) return setup_mode<kRegionA, KMAX, INT_EXP>(x);
+    if (__all_sync(0xffffffffu, r == kRegionB)) return setup_mode<kRegionB, KMAX, INT_EXP>(x);
+    if (__all_sync(0xffffffffu, r == kRegionC)) return setup_mode<kRegionC, KMAX, INT_EXP>(x);
+    return setup<KMAX, INT_EXP>(x);
 }
 
 // One step y_{j+1} = (a_j y_j + s) c_j of the unified recurrence, in the
@@ -218,7 +245,7 @@ __device__ __forceinline__ double step_fp64(const Setup& S, int j, double y) {
 
 // Value number p of the recurrence (p = 0: the anchor; FP64 for p <= NF64,
 // the integer format after), advancing yd / y in place.
-template <int KMAX, int NSTEPS_FP64 = BOYS_FP64_STEPS>
+template <int KMAX, int NSTEPS_FP64 = fp64_steps_for(KMAX)>
 __device__ __forceinline__ double next_value(const Setup& S, int p, double& yd, xf::Xf& y) {
     constexpr int NF64 = NSTEPS_FP64 < KMAX ? NSTEPS_FP64 : KMAX;
     if (p <= NF64) {
@@ -232,9 +259,9 @@ __device__ __forceinline__ double next_value(const Setup& S, int p, double& yd, 
 // F_0..F_KMAX (KMAX <= 32) at x; results in F[0..KMAX].  NSTEPS_FP64 lets a
 // caller whose own work already loads the FP64 pipe move more steps to the
 // integer format; stored and ragged modes use the default and agree bitwise.
-template <int KMAX, int NSTEPS_FP64 = BOYS_FP64_STEPS>
+template <int KMAX, int NSTEPS_FP64 = fp64_steps_for(KMAX), bool INT_EXP = int_exp_for(KMAX, NSTEPS_FP64)>
 __device__ __forceinline__ void eval_point(double x, double (&F)[KMAX + 1]) {
-    const Setup S = setup<KMAX>(x);
+    const Setup S = setup<KMAX, INT_EXP>(x);
     double yd = S.y0d;
     xf::Xf y = S.y0;
     double v[KMAX + 1];
@@ -256,7 +283,7 @@ __device__ __forceinline__ void eval_point(double x, double (&F)[KMAX + 1]) {
 template <int KMAX>
 __device__ __forceinline__ void eval_store(double x, double* __restrict__ col, int64_t ld) {
     constexpr int H = KMAX / 2 + 1;
-    const Setup S = setup<KMAX>(x);
+    const Setup S = setup<KMAX, int_exp_for(KMAX, fp64_steps_for(KMAX))>(x);
     double hold[H];
     double yd = S.y0d;
     xf::Xf y = S.y0;

@@ -44,7 +44,7 @@ __global__ void __launch_bounds__(kBlock) k_pairwise(const double* __restrict__ 
         __syncthreads();
         const int jn = (int)min((int64_t)kBlock, n - j0);
         for (int jj = 0; jj < jn; ++jj) {
-            const fp64::Setup S = fp64::setup_warp<K>(xi + sx[jj]);
+            const fp64::Setup S = fp64::setup_warp<K, true>(xi + sx[jj]);
             double yd = S.y0d;
             xf::Xf yv = S.y0;
             double w = 0.0;

@@ -104,6 +104,60 @@ __device__ __forceinline__ Xf add_prepared(Xf t, XfS s) {
     return u > 0 ? r : zero();
 }
 
+// (a b) / 2^62 for signed Q62 operands whose product stays below 2^125.
+__device__ __forceinline__ long long mul_q62(long long a, long long b) {
+    const long long hi = __mul64hi(a, b);
+    const unsigned long long lo = (unsigned long long)a * (unsigned long long)b;
+    return (long long)(((unsigned long long)hi << 2) | (lo >> 62));
+}
+
+// 2^(-j/256) = m * 2^(e-63) with e = 0 for j = 0 and -1 otherwise.
+static __device__ unsigned long long g_exp2_neg_j256[256] = BOYS_XF_EXP2_NEG_J256_M_INIT;
+
+// e^{-x} for 0 <= x < 32 in this format, on the integer pipes: Tang's
+// table-driven method (ACM TOMS 15(2), 1989) in fixed point.
+//   n = round(256 x / ln 2) from x in Q57, r = x - n ln2/256 in Q62 with
+//   ln2/256 to 2^-89, so |r| <= ln2/512 + 2^-56, exact to 2^-62;
+//   q = e^{-r} - 1 = -r + r^2 (1/2 + r (-1/6 + r (1/24 - r/120))) in Q62:
+//   the inner terms, weighted by r^3 and r^4 (< 2.5e-9), take 32-bit
+//   operands (their 2^-30 truncation costs < 2^-63), r p1 (weight r^2 <
+//   1.9e-6) is formed from two ~31-bit parts (< 2^-61), the rest at full
+//   width; the omitted r^6/720 < 1e-20;
+//   e^{-x} = 2^{-floor(n/256)} * T_{n mod 256} * (1 + q).
+// Relative error below 2^-59.5 (before the conversion to double), checked
+// against an exact emulation and a binary128 reference.
+__device__ __forceinline__ Xf exp_neg(double x) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const int be = (int)((b >> 52) & 0x7FF);
+    const unsigned long long mant = (b & 0xFFFFFFFFFFFFFULL) | 0x10000000000000ULL;
+    const int sh = be - 1018;  // x = mant 2^(be - 1075), x 2^57 = mant 2^sh
+    unsigned long long X = sh >= 0 ? (mant << min(sh, 9)) : (mant >> min(-sh, 63));
+    if (be == 0) X = 0;
+    const unsigned long long t = __umul64hi(X, BOYS_XF_EXP_INVLN2_Q54);  // 256 x / ln2 in Q47
+    const long long n = (long long)((t + (1ULL << 46)) >> 47);
+    // r in Q62, exact to 2^-62: x 2^62 and n (ln2/256) 2^62 can exceed 64 bits
+    // but their difference cannot, so both are formed modulo 2^64
+    const int s62 = be - 1013;  // x 2^62 = mant 2^s62
+    unsigned long long xq = s62 >= 0 ? (mant << min(s62, 14)) : (mant >> min(-s62, 63));
+    if (be == 0) xq = 0;
+    const long long r =
+        (long long)(xq - (unsigned long long)n * (BOYS_XF_EXP_LN2_HI << 5) -
+                    (((unsigned long long)n * BOYS_XF_EXP_LN2_LO + (1ULL << 26)) >> 27));
+    const long long rh = r >> 32;                        // Q30
+    const long long p0 = (long long)BOYS_XF_EXP_24TH_Q62 - rh * (long long)BOYS_XF_EXP_120TH_Q32;
+    const long long p1 = rh * (p0 >> 32) * 4 - (long long)BOYS_XF_EXP_SIXTH_Q62;
+    // r p1 from ~31-bit parts (Q41 x Q33, product < 2^62), error < 2^-41.9
+    const long long p2 = (long long)BOYS_XF_EXP_HALF_Q62 + (((r >> 21) * (p1 >> 29)) >> 12);
+    const long long q = mul_q62(mul_q62(r, r), p2) - r;  // |q| < 0.0014
+    const int j = (int)(n & 255);
+    const unsigned long long P = __umul64hi(__ldg(&g_exp2_neg_j256[j]), (unsigned long long)((1LL << 62) + q));
+    const int lz = __clzll((long long)P);                // 1..3
+    Xf res;
+    res.m = P << lz;
+    res.e = (j ? -1 : 0) + 2 - lz - (int)(n >> 8);
+    return res;
+}
+
 __device__ __forceinline__ Xf odd(int j) { return Xf{c_odd_m[j], c_odd_e[j]}; }        // 2j+1
 __device__ __forceinline__ Xf recip_odd(int l) { return Xf{c_rodd_m[l], c_rodd_e[l]}; }  // 1/(2l+1)
 

@@ -56,3 +56,23 @@ def test_reciprocal_division_rsqrt(fn):
         bound = 1.5
     assert _ulps(got, ref).max() <= bound
     assert np.max(np.abs(got - cuda) / np.spacing(np.abs(cuda))) <= bound + 1.0
+
+
+def test_exp_neg_integer_pipes():
+    """e^{-a} in the 64-bit-significand format (Tang's method in fixed point):
+    relative error below 2^-59, so the significand rounded to nearest double
+    is within 0.5 + 2^-6 ulp of the exact value."""
+    rng = np.random.default_rng(7)
+    k = np.arange(0, 10600)
+    grid = k * (np.log(2.0) / 256)                      # reduction points and their neighbours
+    a = np.concatenate([rng.uniform(0, 32, 300000), np.exp(rng.uniform(np.log(1e-300), np.log(2.0), 50000)),
+                        grid, np.nextafter(grid, 0.0), np.nextafter(grid, 64.0),
+                        [0.0, 5e-324, 1e-310, 2.0 ** -5, np.nextafter(2.0 ** -5, 0.0), 11.899848152108484,
+                         28.98933773882074, np.nextafter(32.0, 0.0)]])
+    a = a[(a >= 0) & (a < 32)]
+    got, at, _ = _run(4, a)
+    assert got[a == 0.0][0] == 1.0
+    ref = np.exp(-a.astype(np.longdouble))
+    assert _ulps(got, ref).max() <= 0.52
+    cuda = torch.exp(-at).cpu().numpy()
+    assert np.max(np.abs(got - cuda) / np.spacing(cuda)) <= 1.0
