@@ -21,7 +21,10 @@
 namespace boys {
 namespace {
 
-constexpr int kBlock = 128;
+#ifndef BOYS_PAIRWISE_BLOCK
+#define BOYS_PAIRWISE_BLOCK 128
+#endif
+constexpr int kBlock = BOYS_PAIRWISE_BLOCK;
 
 template <int K>
 __global__ void __launch_bounds__(kBlock) k_pairwise(const double* __restrict__ x, const double* __restrict__ y,
