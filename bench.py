@@ -51,7 +51,7 @@ HBM_FALLBACK_GBS = 6800.0
 # DRAM bytes per argument of the timed kernel from one ncu capture at N = 2^22
 # (profiles/k_eval_f64_kmax32_eri_mixture.md), scaled to the launch by the
 # arguments it processes; None whenever the kernel changed since that capture.
-TRAFFIC_BYTES_PER_X = 267.3
+TRAFFIC_BYTES_PER_X = 259.1
 
 
 ALL_MODES = ("fused", "fp32", "grad", "pairwise", "ragged")

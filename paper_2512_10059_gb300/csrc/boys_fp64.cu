@@ -11,19 +11,24 @@
 #include "boys_fp64.cuh"
 #include "boys_internal.h"
 
-// Minimum resident blocks per SM for the stored-mode kernel (caps registers).
-#ifndef BOYS_STORED_MIN_BLOCKS
-#define BOYS_STORED_MIN_BLOCKS 10
+// Minimum resident blocks per SM of the stored-mode kernel, which caps its
+// registers: swept on GB300 with the FP64-step table of boys_fp64.cuh, 10
+// blocks (48 registers) up to kmax = 16, 9 (56) up to 24 and 8 (64) above,
+// where more of the recurrence runs in FP64.  BOYS_STORED_MIN_BLOCKS forces
+// one value.
+constexpr int stored_min_blocks(int kmax) {
+#ifdef BOYS_STORED_MIN_BLOCKS
+    return BOYS_STORED_MIN_BLOCKS + 0 * kmax;
+#else
+    return kmax <= 16 ? 10 : (kmax <= 24 ? 9 : 8);
 #endif
+}
 // FP64 recurrence steps and minimum resident blocks of the fused kernel.  Its
 // Horner sum adds KMAX FMAs per argument to the FP64 pipe, so every step runs
 // in the integer format (swept on GB300 at kmax 8..32 x 0..4 FP64 steps: 0
 // was fastest at every kmax).
 #ifndef BOYS_FUSED_FP64_STEPS
 #define BOYS_FUSED_FP64_STEPS 0
-#endif
-#ifndef BOYS_FUSED_INT_EXP
-#define BOYS_FUSED_INT_EXP 1
 #endif
 #ifndef BOYS_FUSED_MIN_BLOCKS
 #define BOYS_FUSED_MIN_BLOCKS 8
@@ -35,7 +40,7 @@ namespace {
 constexpr int kBlock = 128;
 
 template <int KMAX>
-__global__ void __launch_bounds__(kBlock, BOYS_STORED_MIN_BLOCKS) k_eval_f64(const double* __restrict__ x, int64_t n,
+__global__ void __launch_bounds__(kBlock, stored_min_blocks(KMAX)) k_eval_f64(const double* __restrict__ x, int64_t n,
                                                      double* __restrict__ out, int64_t ld) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
@@ -50,7 +55,7 @@ __global__ void __launch_bounds__(kBlock, BOYS_FUSED_MIN_BLOCKS) k_fused_f64(con
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
         double F[KMAX + 1];
-        fp64::eval_point<KMAX, BOYS_FUSED_FP64_STEPS, (BOYS_FUSED_INT_EXP != 0) && BOYS_FUSED_FP64_STEPS == 0>(__ldcs(x + i), F);
+        fp64::eval_point<KMAX, BOYS_FUSED_FP64_STEPS>(__ldcs(x + i), F);
         const double a = -2.0 * __ldcs(rho + i);
         double s = F[KMAX];
 #pragma unroll

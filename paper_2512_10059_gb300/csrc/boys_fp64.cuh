@@ -34,29 +34,31 @@ namespace boys {
 namespace fp64 {
 
 // Recurrence steps that run in FP64; the rest use the 64-bit-significand
-// integer format (boys_xf.cuh).  The set-up (anchors, e^{-x}, the inverse
-// square root) loads the FP64 pipe with the same work for every kmax, while
-// the integer pipes take one step per order: up to about 24 integer steps
-// hide behind the set-up, beyond that each further order is cheaper in FP64.
-// Swept on GB300 (stored mode, kmax 1..32 x 0..8 FP64 steps, 10 blocks per
-// SM): 0 for kmax <= 24, then kmax - 24 up to 28 and kmax - 25 after (7 at
-// kmax = 32).  Defining BOYS_FP64_STEPS forces one value for every kmax.
-// e^{-x} runs on the integer pipes (xf::exp_neg) when no step runs in FP64
-// and the integer pipes still have room: up to kmax = 22 (swept with the split
-// above; at 23 and 24 the integer steps alone nearly fill those pipes).
-#ifndef BOYS_INT_EXP_MAX_KMAX
-#define BOYS_INT_EXP_MAX_KMAX 22
-#endif
-constexpr bool int_exp_for(int kmax, int nsteps_fp64) {
-    return (nsteps_fp64 < kmax ? nsteps_fp64 : kmax) == 0 && kmax <= BOYS_INT_EXP_MAX_KMAX;
-}
-
+// integer format (boys_xf.cuh), and e^{-x} always runs on the integer pipes
+// (xf::exp_neg).  The set-up (Horner, the inverse square root) loads the FP64
+// pipe with the same work at every kmax while the integer pipes take one step
+// per order, so the balance depends on kmax only (the kernels are
+// branch-free, so not on the argument mix).  Swept on GB300 (stored mode,
+// kmax 16..32 x 0..14 FP64 steps): none up to kmax = 18, then about
+// (kmax - 16) / 2, rising to 10 at kmax = 32.  Defining
+// BOYS_FP64_STEPS forces one value for every kmax.
+constexpr int kFp64Steps[33] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0,
+                                0, 0, 1, 1, 2, 3, 3, 4, 4, 5, 6, 7, 7, 8, 9, 10};
 constexpr int fp64_steps_for(int kmax) {
 #ifdef BOYS_FP64_STEPS
     return BOYS_FP64_STEPS + 0 * kmax;
 #else
-    return kmax <= 24 ? 0 : (kmax <= 28 ? kmax - 24 : kmax - 25);
+    return kFp64Steps[kmax];
 #endif
+}
+
+// The integer-pipe e^{-x} is the default everywhere; BOYS_INT_EXP_ALWAYS=0
+// selects the FP64 one (boys_math.cuh) for comparison.
+#ifndef BOYS_INT_EXP_ALWAYS
+#define BOYS_INT_EXP_ALWAYS 1
+#endif
+constexpr bool int_exp_for(int kmax, int nsteps_fp64) {
+    return BOYS_INT_EXP_ALWAYS + 0 * (kmax + nsteps_fp64);
 }
 
 constexpr int kRaN[33] = BOYS_RA_N_INIT;
