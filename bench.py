@@ -150,6 +150,29 @@ def dist_env():
     return ws, rank, local
 
 
+def rank_arguments(n, rank):
+    """Rank r's shard of the headline workload: elements [r n, (r+1) n) of one
+    global argument stream (weak scaling: every rank evaluates n arguments, no
+    data-path collective)."""
+    from paper_2512_10059_gb300 import workloads as W
+    return W.mixture_c2(n, seed=1, start=rank * n)
+
+
+def max_over_ranks(value, dist, device):
+    """The largest of the ranks' values (all ranks receive it)."""
+    if dist is None:
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(world_size, n, kmax, steps, total_ms):
+    """Whole-job F_k values/s: every rank's arguments over the slowest rank's time."""
+    return world_size * n * (kmax + 1) * steps / (total_ms / 1e3)
+
+
 def oracle_sample_rate(kmax, seconds=12.0, threads=0, start=0):
     """The binary128 oracle on host cores over consecutive chunks of the same
     workload until ~`seconds` of wall time; returns (values/s, x evaluated)."""
@@ -214,8 +237,7 @@ def run_ours(args):
     from paper_2512_10059_gb300 import workloads as W
 
     n = 1 << args.n_log2
-    # each rank owns elements [rank*n, (rank+1)*n) of the global argument stream
-    x_host = W.mixture_c2(n, seed=1 + 1000 * rank) if rank else W.mixture_c2(n, seed=1)
+    x_host = rank_arguments(n, rank)
     fpx, fracs = flops_per_x(x_host, KMAX)
     x = torch.from_numpy(x_host).to(dev)
     out = torch.empty((KMAX + 1, n), dtype=torch.float64, device=dev)
@@ -255,12 +277,9 @@ def run_ours(args):
     clocks = clk.summary()
     total_ms = t_start.elapsed_time(t_end)
     launch_ms = [a.elapsed_time(b) for a, b in evs]
-    total_t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-    if dist is not None:
-        dist.all_reduce(total_t, op=dist.ReduceOp.MAX)
-    total_ms = float(total_t.item())
+    total_ms = max_over_ranks(total_ms, dist, dev)
     ms_per_step = total_ms / args.steps
-    value = ws * n * (KMAX + 1) * args.steps / (total_ms / 1e3)
+    value = job_value(ws, n, KMAX, args.steps, total_ms)
 
     # roofline of the evaluation kernel
     hbm_gbs, hbm_src = peaks()

@@ -106,10 +106,12 @@ def mixture_c1(n: int = 65536, seed: int = 0):
     return np.ascontiguousarray(x[perm])
 
 
-def mixture_c2(n: int = 1 << 26, seed: int = 1):
-    """The kmax=32 headline mixture: per-element category from one uniform."""
-    c = uniform01(stream_key(seed, 1), n)
-    u = uniform01(stream_key(seed, 2), n)
+def mixture_c2(n: int = 1 << 26, seed: int = 1, start: int = 0):
+    """The kmax=32 headline mixture: per-element category from one uniform.
+    Elements start..start+n-1 of the stream, so that consecutive ranges (one
+    per GPU) partition one global workload."""
+    c = uniform01(stream_key(seed, 1), n, start)
+    u = uniform01(stream_key(seed, 2), n, start)
     x = np.where(c < 0.4, log_uniform(u, 1e-12, 1e2),
                  np.where(c < 0.8, 60.0 * u, 60.0 + (1e4 - 60.0) * u))
     return np.ascontiguousarray(x)
