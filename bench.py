@@ -6,14 +6,19 @@ drawn from the ERI-shaped mixture (40% log-uniform [1e-12, 1e2], 40% uniform
 (17.7 GB).  Metric: F_k values per second = N * 33 / step time.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--modes fused,fp32,grad,pairwise,ragged | none]
 
 * ``value``     device-resident inputs, CUDA-event timing of K steps on the
                 launching stream, barrier + synchronize on both sides, max
-                over ranks; every rank evaluates its own 2^26 arguments (weak
-                scaling, no data-path collective).
-* ``e2e``       the same metric through the public API with host buffers:
-                each step copies x from pinned host memory, evaluates, and
-                copies all of F back to pinned host memory.
+                over ranks; rank r evaluates elements [r 2^26, (r+1) 2^26) of
+                one argument stream (weak scaling, no data-path collective).
+* ``e2e``       the same metric through the public API with host buffers
+                (boys_eval_host): every step reads x from pinned host memory
+                and writes all of F to pinned host memory over the host link,
+                inside the timed region.
+* ``modes``     the other kernels on their own workloads: fused consumer,
+                FP32 tier, gradient, the paper's Algorithm 2 at N = 2^19,
+                ragged batch (CUDA events, one line each).
 * ``roofline``  the dominant kernel (the FP64 evaluation kernel) against its
                 binding roof: algorithmic FP64 flops (FMA = 2, each divide /
                 exp / rsqrt = 1) over the FP64 peak, or algorithmic HBM bytes

@@ -27,6 +27,8 @@ arguments; names give their sizes):
                    from ``mixture_c1``.
 * ``grad_c5``      N = 2^24 x log-uniform on [1e-10, 1e3]; upstream
                    gradients g_k ~ N(0, 1) (Box-Muller), [17][N].
+* ``pairwise_alg2`` the paper's benchmark inputs (Section III): x ~ U[0, 30],
+                   y, c ~ N(0, 1); N = 2^19 in the paper.
 """
 import numpy as np
 
