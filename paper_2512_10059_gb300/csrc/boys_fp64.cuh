@@ -44,6 +44,21 @@ namespace fp64 {
 // BOYS_FP64_STEPS forces one value for every kmax.
 constexpr int kFp64Steps[33] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0,
                                 0, 0, 1, 1, 2, 3, 3, 4, 4, 5, 6, 7, 7, 8, 9, 10};
+// Numerator and denominator of the anchor evaluated on the integer pipes
+// (xf::fma_i) instead of by FP64 FMAs, for kmax up to these limits (-1: never).
+// At small kmax the FP64 set-up binds while the integer pipes idle: moving
+// the denominator there took 28% off stored mode at kmax <= 2, 23% at 4, 8% at
+// 8, and added 9% at 12; moving the numerator as well overloads the integer
+// pipes at every kmax.  The ragged kernel (many per-kmax bodies resident at
+// once) gained only up to kmax 3 and lost from 5 on (limit 9: +6%), so the
+// limit is 4 (swept on GB300).
+#ifndef BOYS_INT_HORNER_Q_MAXK
+#define BOYS_INT_HORNER_Q_MAXK 4
+#endif
+#ifndef BOYS_INT_HORNER_P_MAXK
+#define BOYS_INT_HORNER_P_MAXK -1
+#endif
+
 constexpr int fp64_steps_for(int kmax) {
 #ifdef BOYS_FP64_STEPS
     return BOYS_FP64_STEPS + 0 * kmax;
@@ -72,6 +87,15 @@ static __constant__ double c_ra_q[33][BOYS_RA_QLEN] = BOYS_RA_Q_INIT;
 // r_B padded with zeros to the r_A row lengths
 static __constant__ double c_rb_p[BOYS_RA_PLEN] = BOYS_RB_P_INIT;
 static __constant__ double c_rb_q[BOYS_RA_QLEN] = BOYS_RB_Q_INIT;
+// the same in the signed integer-significand format (xf::XfI)
+static __constant__ long long c_ra_p_xm[33][BOYS_RA_PLEN] = BOYS_RA_P_XM_INIT;
+static __constant__ int c_ra_p_xe[33][BOYS_RA_PLEN] = BOYS_RA_P_XE_INIT;
+static __constant__ long long c_ra_q_xm[33][BOYS_RA_QLEN] = BOYS_RA_Q_XM_INIT;
+static __constant__ int c_ra_q_xe[33][BOYS_RA_QLEN] = BOYS_RA_Q_XE_INIT;
+static __constant__ long long c_rb_p_xm[BOYS_RA_PLEN] = BOYS_RB_P_XM_INIT;
+static __constant__ int c_rb_p_xe[BOYS_RA_PLEN] = BOYS_RB_P_XE_INIT;
+static __constant__ long long c_rb_q_xm[BOYS_RA_QLEN] = BOYS_RB_Q_XM_INIT;
+static __constant__ int c_rb_q_xe[BOYS_RA_QLEN] = BOYS_RB_Q_XE_INIT;
 
 constexpr int cmax(int a, int b) { return a > b ? a : b; }
 
@@ -132,13 +156,40 @@ __device__ __forceinline__ Setup setup_mode(double x) {
     }
     x = valid ? __longlong_as_double(xb) : quiet_nan();
 
-    // Anchor: r_{A,KMAX} in A, r_B in B (Horner, monic denominators).
-    double p = inA ? c_ra_p[KMAX][NP] : c_rb_p[NP];
+    // Anchor: r_{A,KMAX} in A, r_B in B (Horner, monic denominators), in FP64
+    // or, where the integer pipes have room (small kmax), in xf::XfI.
+    constexpr bool kIntP = KMAX <= BOYS_INT_HORNER_P_MAXK;
+    constexpr bool kIntQ = KMAX <= BOYS_INT_HORNER_Q_MAXK;
+    double p, q;
+    if (kIntP || kIntQ) {
+        const xf::Xf xu = xf::from_double(x);
+        if (kIntP) {
+            xf::XfI t{inA ? c_ra_p_xm[KMAX][NP] : c_rb_p_xm[NP], inA ? c_ra_p_xe[KMAX][NP] : c_rb_p_xe[NP]};
 #pragma unroll
-    for (int i = NP - 1; i >= 0; --i) p = fma(p, x, inA ? c_ra_p[KMAX][i] : c_rb_p[i]);
-    double q = inA ? c_ra_q[KMAX][NQ] : c_rb_q[NQ];
+            for (int i = NP - 1; i >= 0; --i)
+                t = xf::fma_i(t, xu, xf::XfI{inA ? c_ra_p_xm[KMAX][i] : c_rb_p_xm[i],
+                                             inA ? c_ra_p_xe[KMAX][i] : c_rb_p_xe[i]});
+            p = xf::to_double(t);
+        }
+        if (kIntQ) {
+            xf::XfI t{inA ? c_ra_q_xm[KMAX][NQ] : c_rb_q_xm[NQ], inA ? c_ra_q_xe[KMAX][NQ] : c_rb_q_xe[NQ]};
 #pragma unroll
-    for (int i = NQ - 1; i >= 0; --i) q = fma(q, x, inA ? c_ra_q[KMAX][i] : c_rb_q[i]);
+            for (int i = NQ - 1; i >= 0; --i)
+                t = xf::fma_i(t, xu, xf::XfI{inA ? c_ra_q_xm[KMAX][i] : c_rb_q_xm[i],
+                                             inA ? c_ra_q_xe[KMAX][i] : c_rb_q_xe[i]});
+            q = xf::to_double(t);
+        }
+    }
+    if (!kIntP) {
+        p = inA ? c_ra_p[KMAX][NP] : c_rb_p[NP];
+#pragma unroll
+        for (int i = NP - 1; i >= 0; --i) p = fma(p, x, inA ? c_ra_p[KMAX][i] : c_rb_p[i]);
+    }
+    if (!kIntQ) {
+        q = inA ? c_ra_q[KMAX][NQ] : c_rb_q[NQ];
+#pragma unroll
+        for (int i = NQ - 1; i >= 0; --i) q = fma(q, x, inA ? c_ra_q[KMAX][i] : c_rb_q[i]);
+    }
 
     // Arguments beyond 1e300 are clamped there in C (F_0 < 1e-150 and F_k = 0
     // for k > 0 either way); +inf gives exactly 0.

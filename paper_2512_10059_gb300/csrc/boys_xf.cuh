@@ -158,6 +158,39 @@ __device__ __forceinline__ Xf exp_neg(double x) {
     return res;
 }
 
+// Signed form for polynomial evaluation: value = m * 2^(e - 61) with
+// 2^61 <= |m| < 2^62 (one bit of headroom below the sign), or m == 0 for zero
+// (exponent kXfZeroExp).
+struct XfI {
+    long long m;
+    int e;
+};
+
+// One Horner step t * u + c, for t, c signed and u >= 0 normalised (or zero).
+// The product keeps the high 64 bits of t.m * (u.m / 2) (|p| < 2^61), the sum
+// aligns both terms to the larger exponent (|s| < 2^63) and renormalises.
+// Rounding: 2^-60 relative to the larger term per step.
+__device__ __forceinline__ XfI fma_i(XfI t, Xf u, XfI c) {
+    const long long p = __mul64hi(t.m, (long long)(u.m >> 1));
+    const int ep = t.e + u.e + 2;
+    const int E = max(ep, c.e);
+    const long long s = (p >> min(E - ep, 63)) + (c.m >> min(E - c.e, 63));
+    const unsigned long long a = s < 0 ? 0ULL - (unsigned long long)s : (unsigned long long)s;
+    const int lz = __clzll((long long)a);  // >= 1; 64 for zero
+    XfI r;
+    r.m = lz >= 2 ? (long long)((unsigned long long)s << (lz - 2)) : (s >> 1);
+    r.e = lz >= 2 ? E - (lz - 2) : E + 1;
+    return s == 0 ? XfI{0, kXfZeroExp} : r;
+}
+
+// XfI -> double, rounded to nearest (values in the normal range).
+__device__ __forceinline__ double to_double(XfI v) {
+    const unsigned long long a = v.m < 0 ? 0ULL - (unsigned long long)v.m : (unsigned long long)v.m;
+    const unsigned long long bits = ((unsigned long long)(long long)(v.e + 1022) << 52) + ((a + 256) >> 9);
+    const unsigned long long sgn = v.m < 0 ? 0x8000000000000000ULL : 0ULL;
+    return v.m == 0 ? 0.0 : __longlong_as_double((long long)(bits | sgn));
+}
+
 __device__ __forceinline__ Xf odd(int j) { return Xf{c_odd_m[j], c_odd_e[j]}; }        // 2j+1
 __device__ __forceinline__ Xf recip_odd(int l) { return Xf{c_rodd_m[l], c_rodd_e[l]}; }  // 1/(2l+1)
 
