@@ -72,6 +72,28 @@ __device__ __forceinline__ void dispatch(int k, double xv, double* dst, int64_t 
 #undef BOYS_RAGGED_CASE
 }
 
+// Largest s in [lo, hi] with seg_off[s] <= i (seg_off non-decreasing; lo if
+// there is none): a 32-way search by a whole warp.  Each round the lanes
+// probe 32 evenly spaced offsets and a ballot keeps the interval between the
+// last probe at or below i and the next one, so 4096 segments take three
+// dependent loads instead of twelve.  All 32 lanes must call it together;
+// every lane returns the result.
+__device__ __forceinline__ int find_segment_warp(const int64_t* __restrict__ seg_off, int lo, int hi, int64_t i) {
+    const int lane = threadIdx.x & 31;
+    while (hi > lo) {
+        const int span = hi - lo + 1;
+        const int step = (span + 31) / 32;
+        const int probe = lo + lane * step;
+        const bool le = probe <= hi && __ldg(seg_off + probe) <= i;
+        const unsigned m = __ballot_sync(0xffffffffu, le);
+        const int last = m ? 31 - __clz((int)m) : 0;  // none at or below i: stay at lo, as the binary search does
+        lo = lo + last * step;
+        hi = min(hi, lo + step - 1);
+        if (step == 1) break;
+    }
+    return lo;
+}
+
 // Largest s in [lo, hi] with seg_off[s] <= i (seg_off non-decreasing).
 __device__ __forceinline__ int find_segment(const int64_t* __restrict__ seg_off, int lo, int hi, int64_t i) {
     while (lo < hi) {
@@ -95,15 +117,20 @@ __global__ void __launch_bounds__(kMaxBlock, BOYS_RAGGED_MIN_BLOCKS) k_ragged(co
     const int64_t ntiles = (total + per_tile - 1) / per_tile;
     const unsigned lane = threadIdx.x & 31;
     for (;;) {
-        if (threadIdx.x == 0) {
-            const long long t = (long long)atomicAdd(&ws->next_tile, 1ULL);
-            s_tile = t;
+        if (threadIdx.x < 32) {  // warp 0 takes the next tile and finds its segments
+            long long t = 0;
+            if (threadIdx.x == 0) t = (long long)atomicAdd(&ws->next_tile, 1ULL);
+            t = __shfl_sync(0xffffffffu, t, 0);
+            if (threadIdx.x == 0) s_tile = t;
             if (t < ntiles) {
                 const int64_t first = t * per_tile;
                 const int64_t last = min(first + per_tile, total) - 1;
-                const int lo = find_segment(seg_off, 0, nseg - 1, first);
-                s_seg_lo = lo;
-                s_seg_hi = find_segment(seg_off, lo, nseg - 1, last);
+                const int lo = find_segment_warp(seg_off, 0, nseg - 1, first);
+                const int hi = find_segment_warp(seg_off, lo, nseg - 1, last);
+                if (threadIdx.x == 0) {
+                    s_seg_lo = lo;
+                    s_seg_hi = hi;
+                }
             }
         }
         __syncthreads();
