@@ -9,8 +9,11 @@
 // downward, B/C lanes upward; the weights follow) and accumulates
 // z_i += y_j w in FP64.  When x is sorted, the 32 consecutive i of a warp give
 // nearly equal arguments, so almost every warp lies in one region and runs
-// only that region's anchor and special functions (setup_warp); the result is
-// correct for any order.  The recurrence runs entirely in the integer format:
+// only that region's anchor and special functions; the result is correct for
+// any order.  In region C (about half the pairs of the paper's workload) the
+// values F_l = F_0 (2l-1)!! / (2X)^l need no recurrence: the warp evaluates
+// w = F_0 sum_l c_l (2l-1)!! u^l, u = 1/(2X), by Horner in the signed integer
+// format, which takes the w sum off the FP64 pipe.  The recurrence runs entirely in the integer format:
 // this kernel's own FP64 work (the w and z sums) already loads the FP64 pipe.
 #include <array>
 #include <utility>
@@ -31,10 +34,19 @@ __global__ void __launch_bounds__(kBlock) k_pairwise(const double* __restrict__ 
                                                      int64_t n, const double* __restrict__ c,
                                                      double* __restrict__ z) {
     __shared__ double sx[kBlock], sy[kBlock];
+    __shared__ long long s_dm[K + 1];
+    __shared__ int s_de[K + 1];
     double cw[K + 1];
 #pragma unroll
     for (int l = 0; l <= K; ++l) cw[l] = __ldg(c + l);
     const int t = threadIdx.x;
+    if (t <= K) {  // d_l = c_l (2l-1)!! for region C, in the integer format
+        double f = 1.0;
+        for (int m = 0; m < t; ++m) f *= (double)(2 * m + 1);
+        const xf::XfI d = xf::from_double_signed(__ldg(c + t) * f);
+        s_dm[t] = d.m;
+        s_de[t] = d.e;
+    }
     const int64_t i = (int64_t)blockIdx.x * kBlock + t;
     const double xi = i < n ? __ldg(x + i) : 0.0;
     double zi = 0.0;
@@ -47,14 +59,33 @@ __global__ void __launch_bounds__(kBlock) k_pairwise(const double* __restrict__ 
         __syncthreads();
         const int jn = (int)min((int64_t)kBlock, n - j0);
         for (int jj = 0; jj < jn; ++jj) {
-            const fp64::Setup S = fp64::setup_warp<K, true>(xi + sx[jj]);
-            double yd = S.y0d;
-            xf::Xf yv = S.y0;
-            double w = 0.0;
+            const double X = xi + sx[jj];
+            const int r = fp64::region_of(X);
+            double w;
+            if (__all_sync(0xffffffffu, r == fp64::kRegionC)) {
+                // Region C: F_l = F_0 (2l-1)!! u^l with u = 1/(2X), so
+                // w = F_0 sum_l d_l u^l, by Horner in the integer format.
+                const fp64::Setup S = fp64::setup_mode<fp64::kRegionC, K, true>(X);
+                xf::XfI h{s_dm[K], s_de[K]};
 #pragma unroll
-            for (int p = 0; p <= K; ++p) {
-                const double v = fp64::next_value<K, 0>(S, p, yd, yv);
-                w = fma(S.inA ? cw[K - p] : cw[p], v, w);
+                for (int l = K - 1; l >= 0; --l) h = xf::fma_i(h, S.R, xf::XfI{s_dm[l], s_de[l]});
+                w = S.y0d * xf::to_double(h);
+            } else {
+                fp64::Setup S;
+                if (__all_sync(0xffffffffu, r == fp64::kRegionA))
+                    S = fp64::setup_mode<fp64::kRegionA, K, true>(X);
+                else if (__all_sync(0xffffffffu, r == fp64::kRegionB))
+                    S = fp64::setup_mode<fp64::kRegionB, K, true>(X);
+                else
+                    S = fp64::setup<K, true>(X);
+                double yd = S.y0d;
+                xf::Xf yv = S.y0;
+                w = 0.0;
+#pragma unroll
+                for (int p = 0; p <= K; ++p) {
+                    const double v = fp64::next_value<K, 0>(S, p, yd, yv);
+                    w = fma(S.inA ? cw[K - p] : cw[p], v, w);
+                }
             }
             zi = fma(sy[jj], w, zi);
         }

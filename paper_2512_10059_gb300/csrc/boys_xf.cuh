@@ -183,6 +183,17 @@ __device__ __forceinline__ XfI fma_i(XfI t, Xf u, XfI c) {
     return s == 0 ? XfI{0, kXfZeroExp} : r;
 }
 
+// Finite double -> XfI, exactly (subnormals and zero -> zero).
+__device__ __forceinline__ XfI from_double_signed(double d) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(d);
+    const int be = (int)((b >> 52) & 0x7FF);
+    const long long m = (long long)(((b & 0xFFFFFFFFFFFFFULL) | 0x10000000000000ULL) << 9);  // [2^61, 2^62)
+    XfI r;
+    r.m = (b >> 63) ? -m : m;
+    r.e = be - 1023;
+    return be == 0 ? XfI{0, kXfZeroExp} : r;
+}
+
 // XfI -> double, rounded to nearest (values in the normal range).
 __device__ __forceinline__ double to_double(XfI v) {
     const unsigned long long a = v.m < 0 ? 0ULL - (unsigned long long)v.m : (unsigned long long)v.m;

@@ -64,3 +64,18 @@ def test_pairwise_bench_size_sampled():
     hi, lo = oracle.pairwise_rows(x, y, c, rows)
     err = np.abs((got[rows] - hi) - lo)
     assert err.max() <= _tol(y, c, x.size, 12), err.max()
+
+
+@pytest.mark.parametrize("k", [0, 1, 12, 32])
+def test_pairwise_region_c_closed_form(k):
+    """Every x_i + x_j >= 30 lies in region C, where the kernel forms
+    w = F_0 sum_l c_l (2l-1)!! u^l (u = 1/(2X)) instead of running the
+    recurrence; same tolerance."""
+    rng = np.random.default_rng(40 + k)
+    n = 160
+    x = np.sort(rng.uniform(15.0, 30.0, n))
+    y = rng.standard_normal(n)
+    c = rng.standard_normal(k + 1)
+    got = _run(x, y, c)
+    hi, lo = oracle.pairwise(x, y, c)
+    assert np.max(np.abs((got - hi) - lo)) <= _tol(y, c, n, k)
