@@ -24,18 +24,48 @@
 namespace boys {
 namespace {
 
+// In region-A and region-B warps, the first BOYS_PAIRWISE_INT_TERMS values of
+// the recurrence enter w through an integer-format accumulator (xf::fma_i on
+// the recurrence's own values) and the rest through FP64 FMAs, balancing the
+// two pipes: at k = 12, 8 integer terms were fastest (N = 2^19: 13.38 s with
+// none, 12.82 s with 4, 12.63 s with 8, 12.72 s with 10, 13.40 s with all 13).
+#ifndef BOYS_PAIRWISE_INT_TERMS
+#define BOYS_PAIRWISE_INT_TERMS 8
+#endif
 #ifndef BOYS_PAIRWISE_BLOCK
 #define BOYS_PAIRWISE_BLOCK 128
 #endif
 constexpr int kBlock = BOYS_PAIRWISE_BLOCK;
+
+// w = sum_l c_l F_l for a warp whose lanes all lie in region R (A or B):
+// value number p of the recurrence is F_{K-p} in A and F_p in B.
+template <int R, int K>
+__device__ __forceinline__ double w_region(const fp64::Setup& S, const double (&cw)[K + 1],
+                                           const long long* s_cm, const int* s_ce) {
+    constexpr int kInt = BOYS_PAIRWISE_INT_TERMS < K + 1 ? BOYS_PAIRWISE_INT_TERMS : K + 1;
+    double yd = S.y0d;
+    xf::Xf yv = S.y0;
+    double w = 0.0;
+    xf::XfI wi{0, xf::kXfZeroExp};
+#pragma unroll
+    for (int p = 0; p <= K; ++p) {
+        const int l = R == fp64::kRegionA ? K - p : p;
+        const double v = fp64::next_value<K, 0>(S, p, yd, yv);
+        if (p < kInt)
+            wi = xf::fma_i(xf::XfI{s_cm[l], s_ce[l]}, p == 0 ? xf::from_double(S.y0d) : yv, wi);
+        else
+            w = fma(cw[l], v, w);
+    }
+    return kInt > 0 ? w + xf::to_double(wi) : w;
+}
 
 template <int K>
 __global__ void __launch_bounds__(kBlock) k_pairwise(const double* __restrict__ x, const double* __restrict__ y,
                                                      int64_t n, const double* __restrict__ c,
                                                      double* __restrict__ z) {
     __shared__ double sx[kBlock], sy[kBlock];
-    __shared__ long long s_dm[K + 1];
-    __shared__ int s_de[K + 1];
+    __shared__ long long s_dm[K + 1], s_cm[K + 1];
+    __shared__ int s_de[K + 1], s_ce[K + 1];
     double cw[K + 1];
 #pragma unroll
     for (int l = 0; l <= K; ++l) cw[l] = __ldg(c + l);
@@ -46,6 +76,9 @@ __global__ void __launch_bounds__(kBlock) k_pairwise(const double* __restrict__ 
         const xf::XfI d = xf::from_double_signed(__ldg(c + t) * f);
         s_dm[t] = d.m;
         s_de[t] = d.e;
+        const xf::XfI cc = xf::from_double_signed(__ldg(c + t));
+        s_cm[t] = cc.m;
+        s_ce[t] = cc.e;
     }
     const int64_t i = (int64_t)blockIdx.x * kBlock + t;
     const double xi = i < n ? __ldg(x + i) : 0.0;
@@ -70,14 +103,12 @@ __global__ void __launch_bounds__(kBlock) k_pairwise(const double* __restrict__ 
 #pragma unroll
                 for (int l = K - 1; l >= 0; --l) h = xf::fma_i(h, S.R, xf::XfI{s_dm[l], s_de[l]});
                 w = S.y0d * xf::to_double(h);
+            } else if (__all_sync(0xffffffffu, r == fp64::kRegionA)) {
+                w = w_region<fp64::kRegionA, K>(fp64::setup_mode<fp64::kRegionA, K, true>(X), cw, s_cm, s_ce);
+            } else if (__all_sync(0xffffffffu, r == fp64::kRegionB)) {
+                w = w_region<fp64::kRegionB, K>(fp64::setup_mode<fp64::kRegionB, K, true>(X), cw, s_cm, s_ce);
             } else {
-                fp64::Setup S;
-                if (__all_sync(0xffffffffu, r == fp64::kRegionA))
-                    S = fp64::setup_mode<fp64::kRegionA, K, true>(X);
-                else if (__all_sync(0xffffffffu, r == fp64::kRegionB))
-                    S = fp64::setup_mode<fp64::kRegionB, K, true>(X);
-                else
-                    S = fp64::setup<K, true>(X);
+                const fp64::Setup S = fp64::setup<K, true>(X);
                 double yd = S.y0d;
                 xf::Xf yv = S.y0;
                 w = 0.0;
