@@ -454,7 +454,9 @@ def run_ours(args):
                   "segments": int(km3.size), "mean_kmax_weighted": float(np.sum(km3 * lens) / lens.sum()),
                   "hbm_gbs": rbytes / (rms / 1e3) / 1e9,
                   "fp64_frac": rfl / (rms / 1e3) / 1e12 / FP64_PEAK_TFLOPS, "config": plan.config(),
-                  "launch": "one cudaGraphLaunch (workspace memset + persistent kernel)"}
+                  "launch": "one cudaGraphLaunch: workspace memset + " +
+                            ("one kernel per kmax group (parallel graph branches)" if plan.config()["waves"] == 0
+                             else "persistent kernel")}
         plan.close()
         del xt3, ot3, kt3, plan
 

@@ -157,12 +157,15 @@ boys_status boys_ragged_status(const void* workspace, int* bad_kmax, void* strea
 
 /*
  * Ragged plan: fixes the buffers and descriptors of a ragged batch, picks the
- * launch shape (block size 64/128/256, 1 or 2 arguments per thread, 1 or 2
- * resident waves) and captures workspace reset + persistent kernel into a
- * CUDA graph; boys_ragged_plan_launch then replays it with one
- * cudaGraphLaunch.  Creation reads the descriptors back (it synchronises the
- * device), validates them (seg_off[0] = 0, non-decreasing, kmax in [0, 32])
- * and allocates a 256-byte workspace that the plan owns.
+ * launch shape and captures it into a CUDA graph; boys_ragged_plan_launch then
+ * replays it with one cudaGraphLaunch.  Shapes: the persistent kernel (block
+ * size 64/128/256, 1 or 2 arguments per thread, 1 or 2 resident waves), or
+ * waves = 0: one kernel per kmax present, each over a table of tiles of
+ * `block` arguments built at creation, as parallel branches of the graph.
+ * Every shape gives the same bits.  Creation reads the descriptors back (it
+ * synchronises the device), validates them (seg_off[0] = 0, non-decreasing,
+ * kmax in [0, 32]) and allocates a 256-byte workspace, and for waves = 0 the
+ * tile table (16 bytes per tile), that the plan owns.
  *   flags & BOYS_PLAN_AUTOTUNE      time every candidate shape on these very
  *                                   buffers (outputs are overwritten) and
  *                                   keep the fastest; results are cached per
@@ -170,7 +173,8 @@ boys_status boys_ragged_status(const void* workspace, int* bad_kmax, void* strea
  *                                   memory and, if the environment variable
  *                                   BOYS_AUTOTUNE_CACHE names a file, on disk.
  *   flags & BOYS_PLAN_FORCE_CONFIG  take the shape from BOYS_FORCE_CONFIG =
- *                                   "block,xpt,waves" (for tests).
+ *                                   "block,xpt,waves" (for tests; waves 0
+ *                                   selects the per-kmax launches).
  * Without flags the default shape (128, 1, 1) is used.
  */
 #define BOYS_PLAN_AUTOTUNE 1

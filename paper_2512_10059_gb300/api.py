@@ -241,7 +241,8 @@ def ragged_status(workspace: torch.Tensor, stream=None) -> bool:
 
 class RaggedPlan:
     """A ragged batch bound to its buffers, with an autotuned launch shape and a
-    captured CUDA graph (workspace reset + persistent kernel).  ``launch()``
+    captured CUDA graph (workspace reset + persistent kernel, or one kernel per
+    kmax group as parallel branches: ``config()["waves"] == 0``).  ``launch()``
     replays the graph on the current stream.  The tensors are kept alive by
     the plan."""
 

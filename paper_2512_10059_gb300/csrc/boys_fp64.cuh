@@ -49,11 +49,11 @@ constexpr int kFp64Steps[33] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 
 // At small kmax the FP64 set-up binds while the integer pipes idle: moving
 // the denominator there took 28% off stored mode at kmax <= 2, 23% at 4, 8% at
 // 8, and added 9% at 12; moving the numerator as well overloads the integer
-// pipes at every kmax.  The ragged kernel (many per-kmax bodies resident at
-// once) gained only up to kmax 3 and lost from 5 on (limit 9: +6%), so the
-// limit is 4 (swept on GB300).
+// pipes at every kmax.  Ragged plans (one kernel per kmax) gain 3% with limit
+// 8 over limit 4; the persistent ragged kernel used without a plan, whose
+// warps run many per-kmax bodies at once, loses up to 6% (swept on GB300).
 #ifndef BOYS_INT_HORNER_Q_MAXK
-#define BOYS_INT_HORNER_Q_MAXK 4
+#define BOYS_INT_HORNER_Q_MAXK 8
 #endif
 #ifndef BOYS_INT_HORNER_P_MAXK
 #define BOYS_INT_HORNER_P_MAXK -1

@@ -172,6 +172,46 @@ __global__ void __launch_bounds__(kMaxBlock, BOYS_RAGGED_MIN_BLOCKS) k_ragged(co
     }
 }
 
+// ---------------------------------------------- kmax-grouped launches (plans)
+//
+// A plan may instead launch one kernel per kmax present, each over a table of
+// tiles (up to blockDim consecutive arguments of one segment) built on the
+// host when the plan is created.  Every such kernel inlines one evaluation
+// body -- the stored mode's, so the bits are those of boys_eval -- with its
+// own register allocation, no segment search and no per-warp kmax dispatch;
+// the launches are parallel branches of the plan's graph.
+
+struct Tile {
+    int32_t seg;    // segment index
+    int32_t len;    // arguments in this tile (<= blockDim)
+    int64_t start;  // first argument, relative to the segment
+};
+static_assert(sizeof(Tile) == 16, "tile table entries are 16 bytes");
+
+constexpr int grouped_min_blocks(int kmax) { return kmax <= 16 ? 5 : 4; }  // 48 / 64 registers at 256 threads
+
+template <int K>
+__global__ void __launch_bounds__(kMaxBlock, grouped_min_blocks(K)) k_ragged_group(
+        const double* __restrict__ x, const int64_t* __restrict__ seg_off, double* __restrict__ out,
+        const int64_t* __restrict__ out_off, const Tile* __restrict__ tiles, int64_t ntiles) {
+    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const Tile tl = tiles[t];
+        if ((int)threadIdx.x < tl.len) {
+            const int64_t s0 = __ldg(seg_off + tl.seg);
+            const int64_t row = __ldg(seg_off + tl.seg + 1) - s0;
+            const int64_t j = tl.start + threadIdx.x;
+            fp64::eval_store<K>(__ldcs(x + s0 + j), out + __ldg(out_off + tl.seg) + j, row);
+        }
+    }
+}
+
+using GroupFn = void (*)(const double*, const int64_t*, double*, const int64_t*, const Tile*, int64_t);
+
+template <int... K>
+constexpr auto group_table(std::integer_sequence<int, K...>) {
+    return std::array<GroupFn, sizeof...(K)>{&k_ragged_group<K>...};
+}
+
 using KernelFn = void (*)(const double*, const int64_t*, const int32_t*, int, double*, const int64_t*, Workspace*);
 
 inline KernelFn kernel_for(int xpt) { return xpt == 2 ? &k_ragged<2> : &k_ragged<1>; }
@@ -179,7 +219,8 @@ inline KernelFn kernel_for(int xpt) { return xpt == 2 ? &k_ragged<2> : &k_ragged
 struct Config {
     int block = 128;
     int xpt = 1;
-    int waves = 1;  // resident CTAs per SM multiplier for the persistent grid
+    int waves = 1;  // resident CTAs per SM multiplier for the persistent grid;
+                    // 0: one launch per kmax group (plans only; tile = block)
 };
 
 inline int grid_size(const Config& c) {
@@ -213,6 +254,7 @@ const std::vector<Config>& candidates() {
         for (int block : {64, 128, 256})
             for (int xpt : {1, 2})
                 for (int waves : {1, 2}) v.push_back(Config{block, xpt, waves});
+        for (int block : {128, 256}) v.push_back(Config{block, 1, 0});
         return v;
     }();
     return c;
@@ -297,6 +339,12 @@ struct boys_ragged_plan {
     cudaGraph_t graph;
     cudaGraphExec_t exec;
     float tuned_ms;
+    // kmax-grouped launches: host copies of the descriptors and the tile table
+    std::vector<int64_t> off_host;
+    std::vector<int32_t> km_host;
+    ragged::Tile* tiles;
+    int tiles_block;
+    int64_t group_begin[33], group_count[33];
 };
 
 BOYS_API size_t boys_ragged_workspace_size(void) { return 256; }
@@ -328,19 +376,116 @@ BOYS_API boys_status boys_ragged_status(const void* workspace, int* bad_kmax, vo
     return st;
 }
 
-static boys_status capture_graph(boys_ragged_plan* p) {
+// Tile table for tiles of `block` arguments: the tiles of every segment, grouped
+// by the segment's kmax (group k at [group_begin[k], + group_count[k])).
+static boys_status build_tiles(boys_ragged_plan* p, int block) {
+    if (p->tiles && p->tiles_block == block) return BOYS_OK;
+    std::vector<ragged::Tile> tab;
+    for (int k = 0; k <= 32; ++k) {
+        p->group_begin[k] = (int64_t)tab.size();
+        for (int32_t sg = 0; sg < p->nseg; ++sg) {
+            if (p->km_host[sg] != k) continue;
+            const int64_t len = p->off_host[sg + 1] - p->off_host[sg];
+            for (int64_t a = 0; a < len; a += block)
+                tab.push_back(ragged::Tile{sg, (int32_t)std::min<int64_t>(block, len - a), a});
+        }
+        p->group_count[k] = (int64_t)tab.size() - p->group_begin[k];
+    }
+    if (p->tiles) cudaFree(p->tiles);
+    p->tiles = nullptr;
+    p->tiles_block = 0;
+    if (tab.empty()) return BOYS_OK;
+    boys_status st = check_cuda(cudaMalloc((void**)&p->tiles, tab.size() * sizeof(ragged::Tile)), "plan tile table");
+    if (st != BOYS_OK) return st;
+    st = check_cuda(cudaMemcpy(p->tiles, tab.data(), tab.size() * sizeof(ragged::Tile), cudaMemcpyHostToDevice),
+                    "plan tile table upload");
+    if (st == BOYS_OK) p->tiles_block = block;
+    return st;
+}
+
+// Streams and events that fork the kmax groups off the capturing stream and
+// join them back; created before the capture begins (object creation is not
+// a capturable operation) and destroyed after it ends.
+struct GroupFork {
+    cudaEvent_t fork = nullptr;
+    std::vector<int> ks;
+    std::vector<cudaStream_t> streams;
+    std::vector<cudaEvent_t> joins;
+    ~GroupFork() {
+        for (cudaEvent_t j : joins) cudaEventDestroy(j);
+        for (cudaStream_t g : streams) cudaStreamDestroy(g);
+        if (fork) cudaEventDestroy(fork);
+    }
+};
+
+static boys_status prepare_groups(boys_ragged_plan* p, const ragged::Config& c, GroupFork* f) {
+    boys_status st = build_tiles(p, c.block);  // allocates and copies: before any capture
+    if (st != BOYS_OK) return st;
+    st = check_cuda(cudaEventCreateWithFlags(&f->fork, cudaEventDisableTiming), "fork event");
+    for (int k = 0; k <= 32 && st == BOYS_OK; ++k) {
+        if (p->group_count[k] == 0) continue;
+        cudaStream_t g;
+        cudaEvent_t j;
+        st = check_cuda(cudaStreamCreateWithFlags(&g, cudaStreamNonBlocking), "group stream");
+        if (st != BOYS_OK) break;
+        f->streams.push_back(g);
+        st = check_cuda(cudaEventCreateWithFlags(&j, cudaEventDisableTiming), "join event");
+        if (st != BOYS_OK) break;
+        f->joins.push_back(j);
+        f->ks.push_back(k);
+    }
+    return st;
+}
+
+// Records the batch for configuration c on the capturing stream s: the
+// workspace reset, then either the persistent kernel or, for waves == 0, one
+// kernel per kmax group, forked onto their own streams and joined back.
+static boys_status record_launch(boys_ragged_plan* p, const ragged::Config& c, const GroupFork& f, cudaStream_t s) {
+    if (c.waves != 0)
+        return ragged::launch(c, p->x, p->seg_off, p->seg_kmax, p->nseg, p->out, p->out_off, p->ws, s);
+    boys_status st = check_cuda(cudaMemsetAsync(p->ws, 0, sizeof(ragged::Workspace), s), "ragged workspace reset");
+    if (st != BOYS_OK) return st;
+    static constexpr auto tg = ragged::group_table(std::make_integer_sequence<int, 33>{});
+    st = check_cuda(cudaEventRecord(f.fork, s), "fork record");
+    for (size_t q = 0; q < f.ks.size() && st == BOYS_OK; ++q) {
+        const int k = f.ks[q];
+        const int64_t n = p->group_count[k];
+        int per_sm = 1;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tg[k], c.block, 0) != cudaSuccess || per_sm < 1)
+            per_sm = 1;
+        const int64_t grid = std::min<int64_t>(n, (int64_t)sm_count() * per_sm);
+        cudaStreamWaitEvent(f.streams[q], f.fork, 0);
+        tg[k]<<<(unsigned)grid, c.block, 0, f.streams[q]>>>(p->x, p->seg_off, p->out, p->out_off,
+                                                             p->tiles + p->group_begin[k], n);
+        st = check_cuda(cudaGetLastError(), "ragged group launch");
+        cudaEventRecord(f.joins[q], f.streams[q]);
+        cudaStreamWaitEvent(s, f.joins[q], 0);
+    }
+    return st;
+}
+
+static boys_status capture(boys_ragged_plan* p, const ragged::Config& c, cudaGraph_t* graph, cudaGraphExec_t* exec) {
+    *graph = nullptr;
+    *exec = nullptr;
+    GroupFork f;
+    boys_status st = c.waves == 0 ? prepare_groups(p, c, &f) : BOYS_OK;
+    if (st != BOYS_OK) return st;
     cudaStream_t s;
-    boys_status st = check_cuda(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking), "plan stream");
+    st = check_cuda(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking), "plan stream");
     if (st != BOYS_OK) return st;
     st = check_cuda(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal), "begin capture");
     if (st == BOYS_OK) {
-        boys_status lst = ragged::launch(p->cfg, p->x, p->seg_off, p->seg_kmax, p->nseg, p->out, p->out_off, p->ws, s);
+        boys_status lst = record_launch(p, c, f, s);
         cudaGraph_t g = nullptr;
         boys_status est = check_cuda(cudaStreamEndCapture(s, &g), "end capture");
         st = lst != BOYS_OK ? lst : est;
         if (st == BOYS_OK) {
-            p->graph = g;
-            st = check_cuda(cudaGraphInstantiate(&p->exec, g, 0), "graph instantiate");
+            *graph = g;
+            st = check_cuda(cudaGraphInstantiate(exec, g, 0), "graph instantiate");
+            if (st != BOYS_OK) {
+                cudaGraphDestroy(g);
+                *graph = nullptr;
+            }
         } else if (g) {
             cudaGraphDestroy(g);
         }
@@ -349,20 +494,27 @@ static boys_status capture_graph(boys_ragged_plan* p) {
     return st;
 }
 
+static boys_status capture_graph(boys_ragged_plan* p) { return capture(p, p->cfg, &p->graph, &p->exec); }
+
+// Mean time of one replay of configuration c's captured graph (-1 on failure).
 static float time_config(boys_ragged_plan* p, const ragged::Config& c, cudaStream_t s, int reps) {
+    cudaGraph_t g;
+    cudaGraphExec_t e;
+    if (capture(p, c, &g, &e) != BOYS_OK) return -1.0f;
     cudaEvent_t a, b;
     cudaEventCreate(&a);
     cudaEventCreate(&b);
-    ragged::launch(c, p->x, p->seg_off, p->seg_kmax, p->nseg, p->out, p->out_off, p->ws, s);  // warm
+    cudaGraphLaunch(e, s);  // warm
     cudaEventRecord(a, s);
-    for (int r = 0; r < reps; ++r)
-        ragged::launch(c, p->x, p->seg_off, p->seg_kmax, p->nseg, p->out, p->out_off, p->ws, s);
+    for (int r = 0; r < reps; ++r) cudaGraphLaunch(e, s);
     cudaEventRecord(b, s);
     float ms = -1.0f;
     if (cudaEventSynchronize(b) == cudaSuccess) cudaEventElapsedTime(&ms, a, b);
     cudaEventDestroy(a);
     cudaEventDestroy(b);
-    return ms / reps;
+    cudaGraphExecDestroy(e);
+    cudaGraphDestroy(g);
+    return ms > 0 ? ms / reps : -1.0f;
 }
 
 BOYS_API boys_status boys_ragged_plan_create(const double* x, const int64_t* seg_off, const int32_t* seg_kmax,
@@ -391,6 +543,8 @@ BOYS_API boys_status boys_ragged_plan_create(const double* x, const int64_t* seg
     boys_ragged_plan* p = new boys_ragged_plan{};
     p->x = x; p->seg_off = seg_off; p->seg_kmax = seg_kmax; p->nseg = nseg; p->out = out; p->out_off = out_off;
     p->total = off[nseg];
+    p->off_host = off;
+    p->km_host = km;
     st = check_cuda(cudaMalloc((void**)&p->ws, 256), "plan workspace");
     if (st != BOYS_OK) { delete p; return st; }
 
@@ -415,7 +569,7 @@ BOYS_API boys_status boys_ragged_plan_create(const double* x, const int64_t* seg
             cudaStreamDestroy(s);
             p->tuned_ms = best_ms;
             st = check_cuda(cudaGetLastError(), "autotune");
-            if (st != BOYS_OK) { cudaFree(p->ws); delete p; return st; }
+            if (st != BOYS_OK) { boys_ragged_plan_destroy(p); return st; }
             ragged::cache().put(key, best);
         }
         p->cfg = best;
@@ -425,11 +579,11 @@ BOYS_API boys_status boys_ragged_plan_create(const double* x, const int64_t* seg
         const char* f = getenv("BOYS_FORCE_CONFIG");
         ragged::Config c;
         if (f && sscanf(f, "%d,%d,%d", &c.block, &c.xpt, &c.waves) == 3 && (c.block == 64 || c.block == 128 || c.block == 256) &&
-            (c.xpt == 1 || c.xpt == 2) && c.waves >= 1 && c.waves <= 8)
+            (c.xpt == 1 || c.xpt == 2) && c.waves >= 0 && c.waves <= 8)
             p->cfg = c;
     }
     st = capture_graph(p);
-    if (st != BOYS_OK) { cudaFree(p->ws); delete p; return st; }
+    if (st != BOYS_OK) { boys_ragged_plan_destroy(p); return st; }
     *plan = p;
     return BOYS_OK;
 }
@@ -452,6 +606,7 @@ BOYS_API void boys_ragged_plan_destroy(boys_ragged_plan* plan) {
     if (plan->exec) cudaGraphExecDestroy(plan->exec);
     if (plan->graph) cudaGraphDestroy(plan->graph);
     if (plan->ws) cudaFree(plan->ws);
+    if (plan->tiles) cudaFree(plan->tiles);
     delete plan;
 }
 

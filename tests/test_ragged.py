@@ -71,7 +71,8 @@ def test_small_ragged_matches_flat_and_oracle():
         assert np.max(np.abs((blk - hi) - lo)) <= 5e-14 + 1e-27, s
 
 
-@pytest.mark.parametrize("cfg", ["64,1,1", "64,2,2", "128,1,1", "128,2,1", "256,1,2", "256,2,1"])
+@pytest.mark.parametrize("cfg", ["64,1,1", "64,2,2", "128,1,1", "128,2,1", "256,1,2", "256,2,1",
+                                 "128,1,0", "256,1,0", "64,1,0"])
 def test_launch_shapes_bitwise_identical(cfg, monkeypatch):
     x, off, kmax = _small_batch(seed=3, nseg=300)
     xt, ot, kt = _to(DEV, x, off, kmax)
