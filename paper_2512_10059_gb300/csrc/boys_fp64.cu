@@ -2,9 +2,11 @@
 //
 // Stored mode: one thread per argument (grid-stride loop, grid capped at a few
 // waves of resident blocks); KMAX is a template parameter so every loop is
-// unrolled; each order is written to its order-major row as soon as the
-// recurrence produces it, which keeps the register count low enough for the
-// occupancy that hides the integer-pipe latency of the recurrence.
+// unrolled.  A lane keeps only the first half of its orders: from the middle
+// step on every step completes two order-major rows for the whole warp, which
+// are written as full 256-byte segments (fp64::eval_store), and the register
+// count stays low enough for the occupancy that hides the integer-pipe
+// latency of the recurrence.
 #include <array>
 #include <utility>
 

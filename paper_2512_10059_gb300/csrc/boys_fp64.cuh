@@ -20,8 +20,10 @@
 //     C:  a_j = 2j+1,    s = 0,        c_j = 1/(2x)
 // Division by 2l+1 is a multiplication by the rounded constant 1/(2l+1); the
 // paper's zeroth-order error analysis (Appendix B) is indifferent to it.
-// Divisions, 1/(2x), x^{-1/2} and e^{-x} use the FP64-lean routines of
-// boys_math.cuh; region tests compare bit patterns on the integer pipes.
+// The anchors p/q, F_0 in C and 1/(2x) come from one Newton inverse square
+// root (boys_math.cuh); e^{-x}, most recurrence steps and, at small kmax, the
+// denominator q run on the integer pipes (boys_xf.cuh); region tests compare
+// bit patterns on the integer pipes.
 #pragma once
 
 #include <cstdint>
