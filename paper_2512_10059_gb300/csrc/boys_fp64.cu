@@ -15,14 +15,14 @@
 
 // Minimum resident blocks per SM of the stored-mode kernel, which caps its
 // registers: swept on GB300 with the FP64-step table of boys_fp64.cuh, 10
-// blocks (48 registers) up to kmax = 16, 9 (56) up to 24 and 8 (64) above,
-// where more of the recurrence runs in FP64.  BOYS_STORED_MIN_BLOCKS forces
-// one value.
+// blocks (48 registers) up to kmax = 16 (8, 9 and 10 within 0.3% there) and 8
+// (64 registers) above (at kmax 24: 4.61 ms against 4.74 with 9 and 4.88
+// with 10).  BOYS_STORED_MIN_BLOCKS forces one value.
 constexpr int stored_min_blocks(int kmax) {
 #ifdef BOYS_STORED_MIN_BLOCKS
     return BOYS_STORED_MIN_BLOCKS + 0 * kmax;
 #else
-    return kmax <= 16 ? 10 : (kmax <= 24 ? 9 : 8);
+    return kmax <= 16 ? 10 : 8;
 #endif
 }
 // FP64 recurrence steps and minimum resident blocks of the fused kernel.  Its

@@ -41,11 +41,12 @@ namespace fp64 {
 // pipe with the same work at every kmax while the integer pipes take one step
 // per order, so the balance depends on kmax only (the kernels are
 // branch-free, so not on the argument mix).  Swept on GB300 (stored mode,
-// kmax 16..32 x 0..14 FP64 steps): none up to kmax = 18, then about
-// (kmax - 16) / 2, rising to 10 at kmax = 32.  Defining
-// BOYS_FP64_STEPS forces one value for every kmax.
+// N = 2^26, kmax 8/16/24/32 x 0..10 FP64 steps): none up to kmax = 24 (the
+// set-up alone keeps the FP64 pipe busy), 6 at kmax = 32 (5.95 ms against
+// 6.43 ms with none and 6.48 ms with 10).  Defining BOYS_FP64_STEPS forces
+// one value for every kmax.
 constexpr int kFp64Steps[33] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0,
-                                0, 0, 1, 1, 2, 3, 3, 4, 4, 5, 6, 7, 7, 8, 9, 10};
+                                0, 0, 0, 0, 0, 0, 0, 0, 1, 1, 2, 3, 4, 4, 5, 6};
 // Numerator and denominator of the anchor evaluated on the integer pipes
 // (xf::fma_i) instead of by FP64 FMAs, for kmax up to these limits (-1: never).
 // At small kmax the FP64 set-up binds while the integer pipes idle: moving

@@ -4,15 +4,25 @@
 //
 // Why: on GB300 one FP64 instruction costs the issue time of ~60 FP32/INT
 // ones, and the Boys recurrences are 2 FP64 instructions per order.  Carried
-// out in this format they run on the integer pipes with 2^-62 relative
+// out in this format they run on the integer pipes with about 2^-59 relative
 // rounding per operation (finer than FP64's 2^-53) and the full exponent
 // range, so the FP64 accuracy of the method (5e-14 absolute, Appendix B's
 // round-off analysis) is kept; results go back to IEEE doubles by integer
-// assembly of their bit patterns (truncation, < 1 ulp).  Products keep the
-// high 64 bits of the 128-bit significand product; sums align to the larger
-// exponent with 2 bits of headroom and renormalise with a leading-zero count
-// (the product feeding an addition skips its own renormalisation, and the
-// addend e^{-x} is shifted and signed once per argument).
+// assembly of their bit patterns (truncation, < 1 ulp).
+//
+// The operations are built for the recurrence steps y' = (a y + s) c and cost
+// few instructions each:
+//  * products keep the high 64 bits of the 128-bit significand product from
+//    three 32 x 32-bit partial products (mulhi3: at most 2 units of 2^-64
+//    below the exact high half);
+//  * a sum aligns both terms to the larger exponent, one bit below the top,
+//    and renormalises with a 32-bit leading-zero count of the high word: the
+//    recurrences never cancel more than two leading bits (the upward step
+//    (2j+1) F_j - e^{-x} keeps at least 0.36 of (2j+1) F_j on region B, and
+//    the downward step adds two positive terms), so the leading bit of a sum
+//    always lies in the high word;
+//  * the product feeding an addition skips its own renormalisation, and the
+//    addend e^{-x} is shifted and signed once per argument.
 #pragma once
 
 #include <cstdint>
@@ -60,48 +70,63 @@ __device__ __forceinline__ double to_double(Xf v) {
     return v.e < -1022 ? 0.0 : __longlong_as_double((long long)double_bits(v));
 }
 
+// High 64 bits of the 128-bit product a b from three 32 x 32-bit partial
+// products: the low x low product and the low halves of the two cross
+// products are dropped, so the result is at most 2 below the exact high half
+// (never above it).  For a, b >= 2^63 it lies in [2^62, 2^64).
+__device__ __forceinline__ unsigned long long mulhi3(unsigned long long a, unsigned long long b) {
+    const unsigned a0 = (unsigned)a, a1 = (unsigned)(a >> 32);
+    const unsigned b0 = (unsigned)b, b1 = (unsigned)(b >> 32);
+    return (unsigned long long)a1 * b1 + __umulhi(a1, b0) + __umulhi(a0, b1);
+}
+
 __device__ __forceinline__ Xf mul(Xf a, Xf b) {
-    const unsigned long long hi = __umul64hi(a.m, b.m);  // in [2^62, 2^64) for normalised inputs
+    const unsigned long long hi = mulhi3(a.m, b.m);
     const int top = (int)(hi >> 63);
     Xf r;
-    r.m = top ? hi : (hi << 1);
+    r.m = hi << (1 - top);
     r.e = a.e + b.e + top;
     return r;
 }
 
-// Product without renormalisation: the high half of the significand product
-// with the exponent that keeps value = m * 2^(e - 63) exact (m then has up to
-// three leading zero bits).  For operands of an addition, which renormalises.
+// Product without renormalisation: value = m * 2^(e - 63) with m in
+// [2^62, 2^64) (one possible leading zero).  For operands of an addition,
+// which renormalises.
 __device__ __forceinline__ Xf mul_raw(Xf a, Xf b) {
     Xf r;
-    r.m = __umul64hi(a.m, b.m);
+    r.m = mulhi3(a.m, b.m);
     r.e = a.e + b.e + 1;
     return r;
 }
 
-// A signed addend prepared once: value = m * 2^(e - 61), |m| < 2^62.
+// A signed addend prepared once: value = m * 2^(e - 62), |m| < 2^63.
 struct XfS {
     long long m;
     int e;
 };
 
 __device__ __forceinline__ XfS prepare_addend(Xf s, bool negate) {
-    const long long v = (long long)(s.m >> 2);
+    const long long v = (long long)(s.m >> 1);
     return XfS{negate ? -v : v, s.e};
 }
 
-// t + s for t >= 0 (normalised or not) and a prepared signed addend s whose
-// exact sum with t is >= 0; a result at or below zero gives zero.
+// t + s for a raw product t (m in [2^62, 2^64), or zero) and a prepared
+// signed addend s, where either both terms are >= 0 or the exact sum is at
+// least a quarter of t (the recurrences' cases: the sum's leading bit then
+// lies in bits 59..63).  Both terms are aligned to 2^(E - 62), E the larger
+// exponent (t one bit below the top, so two positive terms cannot carry out),
+// added modulo 2^64 and renormalised by a leading-zero count of the high word.
+// A zero sum stays zero (m = 0, exponent near kXfZeroExp).
 __device__ __forceinline__ Xf add_prepared(Xf t, XfS s) {
     const int E = max(t.e, s.e);
-    const long long tm = (long long)(t.m >> min(E - t.e + 2, 63));
-    const long long sm = s.m >> min(E - s.e, 63);  // arithmetic shift keeps the sign
-    const long long u = tm + sm;                   // |tm|, |sm| < 2^62: no overflow
-    const int lz = __clzll(u);
+    const unsigned long long ta = t.m >> min(E - t.e + 1, 63);
+    const long long sa = s.m >> min(E - s.e, 63);  // arithmetic shift keeps the sign
+    const unsigned long long u = ta + (unsigned long long)sa;
+    const int lz = __clz((int)(u >> 32));          // 0..4 for the recurrences; 32 for zero
     Xf r;
-    r.m = (unsigned long long)u << lz;
-    r.e = E + 2 - lz;
-    return u > 0 ? r : zero();
+    r.m = u << lz;
+    r.e = E + 1 - lz;
+    return r;
 }
 
 // (a b) / 2^62 for signed Q62 operands whose product stays below 2^125.
