@@ -48,15 +48,48 @@ KMAX = 32
 N_PER_GPU = 1 << 26
 WORKLOAD = "boys_fp64_stored_kmax32_n2^26_eri_mixture"
 
-# FP64 peak: the recipe's nominal 1.25 TFLOP/s for GB300 is 152 SMs x 2 DFMA per
-# clock per SM x 2 flop x 2.07 GHz = 1.259 TFLOP/s (an in-house DFMA loop measured
-# 1.19 TFLOP/s, 95% of it).  Burst HBM copy bandwidth is driver-measured.
-FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+# FP64 peak: the nominal rate at the SM clock seen during the timed region,
+# SMs (from the device) x 2 DFMA per clock per SM (GB300's FP64 unit) x 2 flop;
+# at 152 SMs and 2.07 GHz that is 1.259 TFLOP/s (an in-house DFMA loop reached
+# 95% of it).  Burst HBM copy bandwidth comes from MEASURED_PEAKS.json; the
+# fallback is the pool's stated 6.8 TB/s.
+DFMA_PER_SM_PER_CLOCK = 2
 HBM_FALLBACK_GBS = 6800.0
 # DRAM bytes per argument of the timed kernel from one ncu capture at N = 2^22
 # (profiles/k_eval_f64_kmax32_eri_mixture.md), scaled to the launch by the
-# arguments it processes; None whenever the kernel changed since that capture.
-TRAFFIC_BYTES_PER_X = 259.1
+# arguments it processes.  Valid only for the kernel sources it was taken on:
+# the bench reports traffic null whenever their SHA-256 differs.
+TRAFFIC_CAPTURE = {"bytes_per_x": 259.1, "sources_sha256": None}
+KERNEL_SOURCES = ("boys_fp64.cu", "boys_fp64.cuh", "boys_xf.cuh", "boys_math.cuh", "boys_coeffs_fp64.h",
+                  "boys_xf_consts.h", "boys_exp_table.h")
+
+
+def kernel_sources_sha256():
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2512_10059_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def fp64_peak_tflops(sm_count, sm_mhz):
+    """Nominal FP64 FMA rate of the device at the given SM clock."""
+    return sm_count * DFMA_PER_SM_PER_CLOCK * 2 * sm_mhz * 1e6 / 1e12
+
+
+def sm_clock_mhz(clocks):
+    """SM clock for the FP64 peak: the median sampled under load, else the
+    device's maximum (nvidia-smi, else MEASURED_PEAKS.json)."""
+    for key in ("sm_mhz", "sm_max_mhz"):
+        v = clocks.get(key) if clocks else None
+        if v:
+            return float(v), f"{key} sampled by nvidia-smi"
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)["sm_max_mhz"]), "sm_max_mhz of MEASURED_PEAKS.json"
+    except Exception:
+        return 2070.0, "GB300 maximum SM clock as stated for the pool (no clock reading available)"
 
 
 ALL_MODES = ("fused", "fp32", "grad", "pairwise", "ragged")
@@ -288,6 +321,10 @@ def run_ours(args):
 
     # roofline of the evaluation kernel
     hbm_gbs, hbm_src = peaks()
+    sm_mhz, clk_src = sm_clock_mhz(clocks)
+    FP64_PEAK_TFLOPS = fp64_peak_tflops(props.multi_processor_count, sm_mhz)
+    fp64_peak_source = (f"FP64 nominal: {props.multi_processor_count} SMs x {DFMA_PER_SM_PER_CLOCK} DFMA/clk x 2 flop "
+                        f"x {sm_mhz:.0f} MHz ({clk_src})")
     avg_launch_s = statistics.mean(launch_ms) / 1e3
     bytes_per_launch = n * 8 * (KMAX + 2)
     flops_per_launch = n * fpx
@@ -295,12 +332,13 @@ def run_ours(args):
     t_fp64 = flops_per_launch / (FP64_PEAK_TFLOPS * 1e12)
     if t_fp64 >= t_hbm:
         roof = {"bound": "alu", "achieved": flops_per_launch / avg_launch_s / 1e12, "peak": FP64_PEAK_TFLOPS,
-                "unit": "TFLOP/s", "peak_source": "FP64 nominal: 152 SM x 2 DFMA/clk x 2 flop x 2.07 GHz"}
+                "unit": "TFLOP/s", "peak_source": fp64_peak_source}
     else:
         roof = {"bound": "hbm", "achieved": bytes_per_launch / avg_launch_s / 1e9, "peak": hbm_gbs,
                 "unit": "GB/s", "peak_source": f"{hbm_src} copy bandwidth"}
     roof["frac"] = roof["achieved"] / roof["peak"]
-    roof["traffic"] = None if TRAFFIC_BYTES_PER_X is None else TRAFFIC_BYTES_PER_X * n
+    same_kernel = TRAFFIC_CAPTURE["sources_sha256"] == kernel_sources_sha256()
+    roof["traffic"] = TRAFFIC_CAPTURE["bytes_per_x"] * n if same_kernel else None
     roof["kernel"] = "k_eval_f64<32>"
     roof["algorithmic_flops_per_x"] = fpx
     roof["algorithmic_bytes_per_x"] = 8 * (KMAX + 2)
@@ -423,9 +461,21 @@ def run_ours(args):
         torch.cuda.synchronize(dev)
         bms = b0.elapsed_time(b1)
         pairs = float(nbig) * nbig
+        # algorithmic FP64 work per pair: Algorithm 1 at k = 12 for the region
+        # of x_i + x_j (mix from 2^20 random pairs), w = sum_l c_l F_l (13 FMA)
+        # and z_i += y_j w (1 FMA)
+        rng = np.random.default_rng(0)
+        xsum = xb[rng.integers(0, nbig, 1 << 20)] + xb[rng.integers(0, nbig, 1 << 20)]
+        pfl, pfr = flops_per_x(xsum, 12)
+        pfl += 2 * 13 + 2
+        ptf = pairs * pfl / (bms / 1e3) / 1e12
         pair = {"n": nbig, "k": 12, "seconds": bms / 1e3, "pairs_per_s": pairs / (bms / 1e3),
                 "value": pairs * 13 / (bms / 1e3), "unit": UNIT, "paper_a100_s_n2^19": 72.0,
-                "n_small": npw, "small_sorted_ms": pms, "small_unsorted_ms": ums}
+                "n_small": npw, "small_sorted_ms": pms, "small_unsorted_ms": ums,
+                "roofline": {"bound": "alu", "algorithmic_flops_per_pair": pfl,
+                             "region_fractions_ABC": [round(f, 4) for f in pfr], "achieved": ptf,
+                             "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": ptf / FP64_PEAK_TFLOPS,
+                             "hbm": "negligible: x, y are re-read from L2/shared memory, 24 B per i"}}
         del xbt, ybt, zbt, cpt
 
     ragged = None
@@ -464,10 +514,25 @@ def run_ours(args):
     # reads x from host memory and writes F to host memory over the host link
     e2e = None
     if not args.skip_e2e:
-        del out
-        torch.cuda.empty_cache()
         xh = torch.from_numpy(x_host).pin_memory()
         oh = torch.empty((KMAX + 1, n), dtype=torch.float64, pin_memory=True)
+
+        def copy_ms(dst, src):
+            c0 = torch.cuda.Event(enable_timing=True)
+            c1 = torch.cuda.Event(enable_timing=True)
+            dst.copy_(src, non_blocking=True)
+            c0.record(stream)
+            dst.copy_(src, non_blocking=True)
+            c1.record(stream)
+            torch.cuda.synchronize(dev)
+            return c0.elapsed_time(c1)
+
+        # the host link's own floor for this step, measured here with copy
+        # engines: x in and all of F out (the link is full duplex)
+        d2h_ms = copy_ms(oh, out)
+        h2d_ms = copy_ms(x, xh)
+        del out
+        torch.cuda.empty_cache()
 
         def e2e_step():
             pb.boys_eval_host(xh, KMAX, out=oh, stream=stream, device=dev)
@@ -488,11 +553,15 @@ def run_ours(args):
         if dist is not None:
             dist.all_reduce(ems, op=dist.ReduceOp.MAX)
         ems = float(ems.item())
+        d2h_bytes = 8 * (KMAX + 1) * n
         e2e = {"value": ws * n * (KMAX + 1) * k_e2e / (ems / 1e3), "unit": UNIT,
-               "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": 8 * (KMAX + 1) * n,
+               "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": d2h_bytes,
                "ms_per_step": ems / k_e2e, "steps": k_e2e,
                "api": "boys_eval_host: pinned host x and F; the kernel moves them over NVLink-C2C",
-               "link_bound_ms": (8 * (KMAX + 1) * n) / 193e9 * 1e3}
+               "link_bound_ms": max(d2h_ms, h2d_ms),
+               "link_measured": {"d2h_ms": d2h_ms, "d2h_gbs": d2h_bytes / (d2h_ms / 1e3) / 1e9,
+                                 "h2d_ms": h2d_ms, "h2d_gbs": 8 * n / (h2d_ms / 1e3) / 1e9,
+                                 "how": "cudaMemcpyAsync of the same bytes, pinned host <-> device, CUDA events"}}
         del xh, oh
 
     cpu = None

@@ -217,9 +217,19 @@ boys_status boys_pairwise(const double* x, const double* y, int64_t n, const dou
  *    `stream` first: calls that overlap on the GPU (other streams, other host
  *    threads) race with each other and produce wrong output.
  *  * No cudaMalloc, cudaFree or other allocating routine is called.
+ *  * A segment whose kmax is outside [0, 32] is skipped (its output block is
+ *    left as it was) and sets the array's error word, which the next call
+ *    clears; boys_ragged_noalloc_status reads it.
  */
 boys_status boys_eval_ragged_noalloc(const double* x, const int64_t* seg_off, const int32_t* seg_kmax,
                                      int32_t nseg, double* out, const int64_t* out_off, void* stream);
+
+/* Error word of the latest boys_eval_ragged_noalloc call on the current
+ * device, read after the work enqueued on `stream` so far (synchronises
+ * `stream`; copies 8 bytes from the static array, allocates nothing):
+ * *bad_kmax = 1 if a segment had kmax outside [0, 32], else 0.  Like the
+ * evaluation itself it has no counterpart in the paper. */
+boys_status boys_ragged_noalloc_status(int* bad_kmax, void* stream);
 
 #ifdef __cplusplus
 }

@@ -45,6 +45,7 @@ def _declare(lib):
         "boys_ragged_plan_config": (i32, [vp, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32)]),
         "boys_ragged_plan_destroy": (None, [vp]),
         "boys_eval_ragged_noalloc": (i32, [vp, vp, vp, i32, vp, vp, vp]),
+        "boys_ragged_noalloc_status": (i32, [ctypes.POINTER(i32), vp]),
         "boys_pairwise": (i32, [vp, vp, i64, vp, i32, vp, vp]),
     }
     SIGNATURES.update(sig)

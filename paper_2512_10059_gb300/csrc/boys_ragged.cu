@@ -16,6 +16,7 @@
 #include <algorithm>
 #include <array>
 #include <chrono>
+#include <cstddef>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -680,4 +681,20 @@ BOYS_API boys_status boys_eval_ragged_noalloc(const double* x, const int64_t* se
     if (st != BOYS_OK) return st;
     ragged::k_ragged<1><<<grid, 128, 0, s>>>(x, seg_off, seg_kmax, nseg, out, out_off, (ragged::Workspace*)scratch);
     return check_cuda(cudaGetLastError(), "boys_eval_ragged_noalloc launch");
+}
+
+// The error word of the static array on the current device, read after the
+// stream's work so far; copying from the symbol needs no device address and
+// no allocation.
+BOYS_API boys_status boys_ragged_noalloc_status(int* bad_kmax, void* stream) {
+    if (!bad_kmax) return fail(BOYS_ERR_INVALID_ARG, "boys_ragged_noalloc_status: NULL pointer");
+    unsigned long long err = 0;
+    cudaStream_t s = (cudaStream_t)stream;
+    boys_status st = check_cuda(cudaMemcpyFromSymbolAsync(&err, ragged::g_noalloc_scratch, sizeof(err),
+                                                          offsetof(ragged::Workspace, error), cudaMemcpyDeviceToHost, s),
+                                "boys_ragged_noalloc_status copy");
+    if (st != BOYS_OK) return st;
+    st = check_cuda(cudaStreamSynchronize(s), "boys_ragged_noalloc_status sync");
+    *bad_kmax = err ? 1 : 0;
+    return st;
 }

@@ -552,15 +552,32 @@ static float horner_f(const std::vector<float>& c, float x) {
     return v;
 }
 
-// Algorithm 1 in FP32 with the kernel's operation order; F[0..kmax].
+// The kernel's e^{-x}: Cody and Waite's reduction x = n ln2 + r and the
+// degree-7 Taylor polynomial of e^{-r}, in the same float operations.
+static float exp_neg_f(float x) {
+    const float t = fmaf(x, 1.4426950216293335f, 12582912.0f);
+    const float n = t - 12582912.0f;
+    float r = fmaf(-n, 0.693115234375f, x);
+    r = fmaf(-n, 3.194618329871446e-05f, r);
+    float p = -1.98412701e-04f;
+    for (float c : {1.38888892e-03f, -8.33333377e-03f, 4.16666679e-02f, -1.66666672e-01f, 0.5f, -1.0f, 1.0f})
+        p = fmaf(p, r, c);
+    return ldexpf(p, -(int)n);
+}
+
+// Algorithm 1 in FP32 with the kernel's operation order; F[0..kmax].  The
+// kernel's quotient, reciprocal and inverse square root (hardware seed plus
+// one correction, within about an ulp) are modelled by the correctly rounded
+// operations.
 static void eval_f32(const Tier& T, float x, float* F) {
     const int K = T.kmax;
     const bool inA = x < T.x0, inC = x >= T.x1;
+    const float r = 1.0f / sqrtf(x);
     float y0;
-    if (inC) y0 = 0.88622692545275801365f / sqrtf(x);
+    if (inC) y0 = 0.88622692545275801365f * r;
     else if (inA) y0 = horner_f(T.ap, x) / horner_f(T.aq, x);
     else y0 = horner_f(T.bp, x) / horner_f(T.bq, x);
-    const float e = inC ? 0.0f : expf(-x);
+    const float e = inC ? 0.0f : exp_neg_f(x);
     const float two_x = x + x, inv2x = 1.0f / two_x;
     float y[40];
     y[0] = y0;

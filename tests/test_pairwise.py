@@ -55,15 +55,36 @@ def test_pairwise_order_invariant():
     assert np.max(np.abs(z1[perm] - z2)) <= _tol(y, c, 1000, 12)
 
 
-def test_pairwise_bench_size_sampled():
-    """N = 2^17 (the size bench.py times), sorted x on [0, 30], k = 12: eight
-    rows against the oracle."""
-    x, y, c = W.pairwise_alg2(1 << 17, 12, seed=8, sort=True)
+@pytest.mark.parametrize("log2n,nrows", [(17, 8), (19, 3)])
+def test_pairwise_bench_sizes_sampled(log2n, nrows):
+    """The two launches bench.py times: N = 2^17 and the paper's N = 2^19,
+    sorted x on [0, 30], k = 12, seed 8; sampled rows against the oracle."""
+    x, y, c = W.pairwise_alg2(1 << log2n, 12, seed=8, sort=True)
     got = _run(x, y, c)
-    rows = np.random.default_rng(0).choice(x.size, 8, replace=False)
+    rows = np.random.default_rng(log2n).choice(x.size, nrows, replace=False)
     hi, lo = oracle.pairwise_rows(x, y, c, rows)
     err = np.abs((got[rows] - hi) - lo)
     assert err.max() <= _tol(y, c, x.size, 12), err.max()
+
+
+@pytest.mark.parametrize("k,sort", [(12, True), (12, False), (32, True), (3, False)])
+def test_pairwise_one_hot_pins_each_pair(k, sort):
+    """y = e_m makes z_i = sum_l c_l F_l(x_i + x_m): every output pins one
+    pair, so the bound is the per-pair one, 5e-14 sum_l|c_l| plus the rounding
+    of the k+1-term sum, independent of n.  The m are chosen so that x_i + x_m
+    covers regions A, B and C (and the region-C Horner form in sorted warps)."""
+    n = 640
+    x, _, c = W.pairwise_alg2(n, k, seed=70 + k, sort=sort)
+    sc = np.abs(c).sum()
+    tol = 5e-14 * sc + 2.0 ** -53 * (k + 2) * sc + 1e-27
+    order = np.argsort(x)
+    for m in (order[0], order[n // 3], order[2 * n // 3], order[-1]):
+        y = np.zeros(n)
+        y[m] = 1.0
+        got = _run(x, y, c)
+        hi, lo = oracle.pairwise(x, y, c)
+        err = np.abs((got - hi) - lo)
+        assert err.max() <= tol, (m, err.max(), tol)
 
 
 @pytest.mark.parametrize("k", [0, 1, 12, 32])
