@@ -65,6 +65,7 @@ int boys_kmax_limit(void);
  * FP64 elementary functions elementwise, out[i] = f(a[i]):
  *   fn 0: e^{-a} (0 <= a <= 700)  1: 1/a  2: b[i]/a  3: a^{-1/2}   (a normal)
  *   fn 4: e^{-a} on the integer pipes (0 <= a < 32), rounded to nearest double
+ *   fn 5: a^{-1/2} on the integer pipes (a normal), rounded to nearest double
  * so that their accuracy can be measured against CUDA's functions.
  */
 boys_status boys_diag_math(int fn, const double* a, const double* b, int64_t n, double* out, void* stream);

@@ -20,8 +20,8 @@ __global__ void k_diag_math(int fn, const double* __restrict__ a, const double* 
             case 1: r = dmath::rcp(v); break;
             case 2: r = dmath::div(b[i], v); break;
             case 3: r = dmath::rsqrt(v); break;
-            default: {  // integer-pipe e^{-v}, its 64-bit significand rounded to nearest
-                const xf::Xf e = xf::exp_neg(v);
+            default: {  // integer pipes: e^{-v} (4) or v^{-1/2} (5), the 64-bit significand rounded to nearest
+                const xf::Xf e = fn == 4 ? xf::exp_neg(v) : xf::rsqrt(xf::from_double(v));
                 const double hi = (double)(e.m >> 11), lo = (double)(e.m & 0x7FF);
                 r = ldexp(hi + lo * 0x1p-11, e.e - 52);
                 break;
@@ -36,7 +36,7 @@ __global__ void k_diag_math(int fn, const double* __restrict__ a, const double* 
 
 BOYS_API boys_status boys_diag_math(int fn, const double* a, const double* b, int64_t n, double* out, void* stream) {
     using namespace boys;
-    if (fn < 0 || fn > 4) return fail(BOYS_ERR_INVALID_ARG, "boys_diag_math: fn=%d outside [0, 4]", fn);
+    if (fn < 0 || fn > 5) return fail(BOYS_ERR_INVALID_ARG, "boys_diag_math: fn=%d outside [0, 5]", fn);
     if (n < 0) return fail(BOYS_ERR_INVALID_ARG, "boys_diag_math: n < 0");
     if (n == 0) return BOYS_OK;
     if (!a || !out || (fn == 2 && !b)) return fail(BOYS_ERR_INVALID_ARG, "boys_diag_math: NULL pointer");

@@ -20,10 +20,11 @@
 //     C:  a_j = 2j+1,    s = 0,        c_j = 1/(2x)
 // Division by 2l+1 is a multiplication by the rounded constant 1/(2l+1); the
 // paper's zeroth-order error analysis (Appendix B) is indifferent to it.
-// The anchors p/q, F_0 in C and 1/(2x) come from one Newton inverse square
-// root (boys_math.cuh); e^{-x}, most recurrence steps and, at small kmax, the
-// denominator q run on the integer pipes (boys_xf.cuh); region tests compare
-// bit patterns on the integer pipes.
+// The anchors p/q, F_0 in C and 1/(2x) come from one inverse square root in
+// the 64-bit-significand format; it, e^{-x}, most recurrence steps and, at
+// small kmax, the denominator q run on the integer pipes (boys_xf.cuh), and
+// region tests compare bit patterns there too: the FP64 pipe evaluates the
+// Horner sums and whatever recurrence steps the balance gives it.
 #pragma once
 
 #include <cstdint>
@@ -37,16 +38,14 @@ namespace fp64 {
 
 // Recurrence steps that run in FP64; the rest use the 64-bit-significand
 // integer format (boys_xf.cuh), and e^{-x} always runs on the integer pipes
-// (xf::exp_neg).  The set-up (Horner, the inverse square root) loads the FP64
-// pipe with the same work at every kmax while the integer pipes take one step
-// per order, so the balance depends on kmax only (the kernels are
-// branch-free, so not on the argument mix).  Swept on GB300 (stored mode,
-// N = 2^26, kmax 8/16/24/32 x 0..10 FP64 steps): none up to kmax = 24 (the
-// set-up alone keeps the FP64 pipe busy), 6 at kmax = 32 (5.95 ms against
-// 6.43 ms with none and 6.48 ms with 10).  Defining BOYS_FP64_STEPS forces
-// one value for every kmax.
-constexpr int kFp64Steps[33] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0,
-                                0, 0, 0, 0, 0, 0, 0, 0, 1, 1, 2, 3, 4, 4, 5, 6};
+// (xf::exp_neg).  The set-up loads the FP64 pipe with the Horner sums only,
+// the same work at every kmax, while the integer pipes take one step per
+// order, so the balance depends on kmax only (the kernels are branch-free, so
+// not on the argument mix).  Swept on GB300 (stored mode, N = 2^26): every
+// step in FP64 up to kmax = 8, then 4 at 16, 8 at 24 and 12 or more at 32.
+// Defining BOYS_FP64_STEPS forces one value for every kmax.
+constexpr int kFp64Steps[33] = {0, 1, 2, 3, 4, 5, 6, 7, 8, 7, 7, 6, 6, 5, 5, 4, 4,
+                                5, 5, 6, 6, 7, 7, 8, 8, 9, 9, 10, 10, 11, 11, 12, 12};
 // Numerator and denominator of the anchor evaluated on the integer pipes
 // (xf::fma_i) instead of by FP64 FMAs, for kmax up to these limits (-1: never).
 // At small kmax the FP64 set-up binds while the integer pipes idle: moving
@@ -134,15 +133,16 @@ enum Region { kRegionA = 0, kRegionB = 1, kRegionC = 2, kRegionNone = 3 };
 // MODE = kRegionA/B/C is for x known to be valid and in that region, where
 // the other regions' work folds away at compile time.
 //
-// Branch-free, one inverse square root serves all three anchors (one Newton
-// iteration pair instead of three): r = z^{-1/2} with z = q^2 in A, (2x q)^2
-// in B and x in C, so that
-//   A: p/q = sign(q) p r,  B: p/q = sign(q) 2x p r,  1/(2x) = |q| r,
-//   C: F_0 = (sqrt(pi)/2) r,  1/(2x) = r (r/2).
-// (q keeps one sign on each region's interval and |q| lies in [2e7, 7e16]
-// for every table row, so the squares stay normal.)  A single region takes
-// its cheapest form instead: the Newton quotient p/q in A and B, 1/(2x) by a
-// Newton reciprocal in B, and r (r/2) from the inverse square root in C.
+// Branch-free, one inverse square root serves all three anchors: r = z^{-1/2}
+// with z = q^2 in A, (2x q)^2 in B and x in C, so that
+//   A: p/q = |p| r,  B: p/q = 2x |p| r,  1/(2x) = |q| r,
+//   C: F_0 = (sqrt(pi)/2) r,  1/(2x) = r (r/2)
+// (p and q have one common sign on each region's interval, since p/q
+// approximates a positive F_k, and |q| lies in [2e7, 7e16] for every table
+// row).  All of it runs in the 64-bit-significand format on the integer pipes
+// (xf::rsqrt, xf::mul), about 2^-58 relative in all, against 3 ulp for the
+// same chain in FP64, which took 14 FP64 instructions per argument.  A single
+// region (MODE) keeps only its own products.
 template <int MODE, int KMAX, bool INT_EXP = false>
 __device__ __forceinline__ Setup setup_mode(double x) {
     static_assert(KMAX >= 0 && KMAX <= 32, "tables cover orders 0..32");
@@ -197,27 +197,33 @@ __device__ __forceinline__ Setup setup_mode(double x) {
     // Arguments beyond 1e300 are clamped there in C (F_0 < 1e-150 and F_k = 0
     // for k > 0 either way); +inf gives exactly 0.
     const bool huge = xb > kBits1e300 && xb <= kBitsInf;
-    const double xr = huge ? 1e300 : x;
-    const double two_x = x + x;
-    double rat, asym0, inv2x;
+    const xf::Xf X = xf::from_double(huge ? 1e300 : x);
+    const xf::Xf X2{X.m, X.e + 1};  // 2x, exact
+    // The anchors from one inverse square root in the 64-bit-significand
+    // format (integer pipes): r = z^{-1/2} with z = q^2 (A), (2x q)^2 (B), x (C).
+    // p/q > 0 on both regions, so magnitudes suffice (from_double drops signs).
+    const xf::Xf P = xf::from_double(p);
+    const xf::Xf Q = xf::from_double(q);
+    xf::Xf y0, R;
     if (MODE == kRegionNone) {
-        const double t = inA ? q : two_x * q;
-        const double r = dmath::rsqrt(inC ? xr : t * t);
-        const double ps =
-            __longlong_as_double(__double_as_longlong(p) ^ (__double_as_longlong(t) & (long long)0x8000000000000000ULL));
-        rat = r * (inA ? ps : ps * two_x);
-        asym0 = (xb == kBitsInf) ? 0.0 : kSqrtPiOver2 * r;
-        inv2x = r * (inC ? 0.5 * r : fabs(q));
-    } else if (MODE == kRegionC) {
-        const double r = dmath::rsqrt(xr);
-        rat = 0.0;
-        asym0 = (xb == kBitsInf) ? 0.0 : kSqrtPiOver2 * r;
-        inv2x = r * (0.5 * r);
+        const xf::Xf tq = inA ? Q : xf::mul(X2, Q);
+        const xf::Xf r = xf::rsqrt(inC ? X : xf::mul(tq, tq));
+        y0 = xf::mul(inA ? P : (inC ? xf::sqrt_pi_over_2() : xf::mul(X2, P)), r);
+        R = xf::mul(inC ? xf::Xf{r.m, r.e - 1} : Q, r);
+    } else if (MODE == kRegionA) {
+        y0 = xf::mul(P, xf::rsqrt(xf::mul(Q, Q)));
+        R = xf::zero();
+    } else if (MODE == kRegionB) {
+        const xf::Xf tq = xf::mul(X2, Q);
+        const xf::Xf r = xf::rsqrt(xf::mul(tq, tq));
+        y0 = xf::mul(xf::mul(X2, P), r);
+        R = xf::mul(Q, r);
     } else {
-        rat = dmath::div(p, q);
-        asym0 = 0.0;
-        inv2x = MODE == kRegionB ? dmath::rcp(two_x) : 0.0;
+        const xf::Xf r = xf::rsqrt(X);
+        y0 = xf::mul(xf::sqrt_pi_over_2(), r);
+        R = xf::mul(xf::Xf{r.m, r.e - 1}, r);
     }
+    if (xb == kBitsInf) y0 = xf::zero();
     // e^{-x}: on the integer pipes, straight into the recurrence's format, when
     // no step runs in FP64 (the FP64 copy is then only assembled if used)
     double e;
@@ -233,16 +239,15 @@ __device__ __forceinline__ Setup setup_mode(double x) {
     Setup S;
     S.valid = valid;
     S.inA = inA;
-    S.y0d = inC ? asym0 : rat;
-    S.two_x = two_x;
+    S.y0 = y0;
+    S.y0d = xf::to_double(y0);
+    S.X2 = X2;
+    S.two_x = xf::to_double(X2);
     S.sd = inC ? 0.0 : (inA ? e : -e);
-    S.inv2x = inv2x;
-    S.y0 = xf::from_double(S.y0d);
-    S.X2 = xf::from_double(x);
-    S.X2.e += 1;                                     // 2x, exact
+    S.R = R;
+    S.inv2x = xf::to_double(R);
     S.Ev = inC ? xf::zero() : E;                     // zero in region C
     S.Es = xf::prepare_addend(S.Ev, !inA);
-    S.R = xf::from_double(inv2x);
     return S;
 }
 

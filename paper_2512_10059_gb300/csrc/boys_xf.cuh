@@ -129,6 +129,38 @@ __device__ __forceinline__ Xf add_prepared(Xf t, XfS s) {
     return r;
 }
 
+// z^{-1/2} for normalised z > 0 (exponent within +-2^30), relative error
+// below 2^-59.  Seed: rsqrt.approx.ftz.f32 of the top 23 bits of z's
+// significand with the exponent's parity (z = s 2^(2h), s in [1, 4)), so the
+// seed y has |1 - z y^2| < 2^-21 (any |d| < 2^-19 keeps the fixed-point
+// ranges below); then one third-order Newton step
+//   y' = y (1 + d/2 + 3 d^2/8),  d = 1 - z y^2,
+// whose truncation error is 5 d^3/16 < 2^-64.  d is formed in Q62 fixed
+// point (z y^2 is within 2^-19 of 1), d^2 from its top 31 bits.
+__device__ __forceinline__ Xf rsqrt(Xf z) {
+    const int h = z.e >> 1;  // floor(e / 2)
+    const float s = __int_as_float(((127 + (z.e & 1)) << 23) | (int)((z.m >> 40) & 0x7FFFFF));
+    float sf;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(sf) : "f"(s));
+    const int sb = __float_as_int(sf);
+    const Xf y{(unsigned long long)((sb & 0x7FFFFF) | 0x800000) << 40, ((sb >> 23) & 0xFF) - 127 - h};
+    const Xf w = mul(mul(y, y), z);                                   // 1 - d, exponent 0 or -1
+    const unsigned long long W = w.m >> min(max(1 - w.e, 0), 63);     // in Q62
+    const long long D = (long long)(1ULL << 62) - (long long)W;       // d in Q62, |D| < 2^43
+    const int Ds = (int)(D >> 12);
+    const unsigned long long D2 = (unsigned long long)((long long)Ds * Ds);  // d^2 in Q38
+    const long long C = (D >> 1) + (long long)((3 * D2) >> 41);       // d/2 + 3 d^2/8 in Q62
+    const unsigned long long Cm = (unsigned long long)(C < 0 ? -C : C);
+    const unsigned long long corr = mulhi3(y.m, Cm << 21) >> 20;      // (y.m / 2) |C| / 2^62
+    const unsigned long long hm = y.m >> 1;
+    const unsigned long long u = C < 0 ? hm - corr : hm + corr;       // leading bit 61..63
+    const int lz = __clz((int)(u >> 32));
+    return Xf{u << lz, y.e + 1 - lz};
+}
+
+// sqrt(pi)/2, the factor of the asymptotic F_0 of region C.
+__device__ __forceinline__ Xf sqrt_pi_over_2() { return Xf{BOYS_XF_SQRTPI_2_M, -1}; }
+
 // (a b) / 2^62 for signed Q62 operands whose product stays below 2^125.
 __device__ __forceinline__ long long mul_q62(long long a, long long b) {
     const long long hi = __mul64hi(a, b);

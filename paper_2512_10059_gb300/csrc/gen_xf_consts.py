@@ -31,7 +31,8 @@ for name, fn in (("ODD", odd), ("RECIP_ODD", recip)):
 
 # e^{-x} on the integer pipes (Tang's method in fixed point, 256 subintervals):
 # T_j = 2^(-j/256) as (m, e); 256/ln2 in Q54; ln2/256 in Q89 split into the
-# high bits (>> 32) and the low 32 bits; 1/2, 1/6, 1/24 in Q62 and 1/120 in Q32.
+# high bits (>> 32) and the low 32 bits; 1/2, 1/6, 1/24 in Q62 and 1/120 in Q32;
+# and sqrt(pi)/2 (pi to 63 digits) in Q64.
 from decimal import Decimal, getcontext, ROUND_HALF_EVEN
 
 getcontext().prec = 60
@@ -63,6 +64,10 @@ consts = {
     "BOYS_XF_EXP_24TH_Q62": q(Decimal(1) / 24, 62),
     "BOYS_XF_EXP_120TH_Q32": q(Decimal(1) / 120, 32),
 }
+# sqrt(pi)/2 = m * 2^(-1-63), the asymptotic F_0 factor of region C
+PI = Decimal("3.14159265358979323846264338327950288419716939937510582097494459")
+consts["BOYS_XF_SQRTPI_2_M"] = q(PI.sqrt() / 2, 64)
+assert (1 << 63) <= consts["BOYS_XF_SQRTPI_2_M"] < (1 << 64)
 assert consts["BOYS_XF_EXP_INVLN2_Q54"] < (1 << 63)
 print("// Tang's e^{-x} in fixed point: T_j = 2^(-j/256) = m * 2^(e-63), and the")
 print("// reduction and polynomial constants (see xf::exp_neg).")

@@ -1,5 +1,7 @@
-"""The library's FP64 elementary functions (Tang exp, Newton reciprocal and
-division, Newton rsqrt) against CUDA's functions and a long double reference."""
+"""The library's elementary functions (FP64: Tang exp, Newton reciprocal and
+division, Newton rsqrt; integer pipes: Tang exp in fixed point and the
+third-order Newton inverse square root) against CUDA's functions and a long
+double reference (binary128 on the AArch64 GPU hosts)."""
 import numpy as np
 import pytest
 import torch
@@ -75,4 +77,21 @@ def test_exp_neg_integer_pipes():
     ref = np.exp(-a.astype(np.longdouble))
     assert _ulps(got, ref).max() <= 0.52
     cuda = torch.exp(-at).cpu().numpy()
+    assert np.max(np.abs(got - cuda) / np.spacing(cuda)) <= 1.0
+
+
+def test_rsqrt_integer_pipes():
+    """a^{-1/2} in the 64-bit-significand format (rsqrt.approx.f32 seed of the
+    top 23 significand bits, one third-order Newton step): relative error
+    below 2^-59, so the significand rounded to nearest double is within
+    0.5 + 2^-6 ulp.  Both exponent parities, powers of two, the seed's
+    mantissa boundaries and the anchors' range (q^2 up to 5e33, x up to 1e300)."""
+    rng = np.random.default_rng(11)
+    a = np.concatenate([np.exp(rng.uniform(-690, 690, 300000)), rng.uniform(1.0, 4.0, 100000),
+                        2.0 ** np.arange(-1000, 1000), np.nextafter(2.0 ** np.arange(-60, 60), 0.0),
+                        1.0 + 2.0 ** -23 * np.arange(0, 4096), [1e300, 5e33, 4e14, 28.98933773882074]])
+    got, at, _ = _run(5, a)
+    ref = 1 / np.sqrt(a.astype(np.longdouble))
+    assert _ulps(got, ref).max() <= 0.52
+    cuda = torch.rsqrt(at).cpu().numpy()
     assert np.max(np.abs(got - cuda) / np.spacing(cuda)) <= 1.0
