@@ -19,11 +19,12 @@ drawn from the ERI-shaped mixture (40% log-uniform [1e-12, 1e2], 40% uniform
 * ``modes``     the other kernels on their own workloads: fused consumer,
                 FP32 tier, gradient, the paper's Algorithm 2 at N = 2^19,
                 ragged batch (CUDA events, one line each).
-* ``roofline``  the dominant kernel (the FP64 evaluation kernel) against its
-                binding roof: algorithmic FP64 flops (FMA = 2, each divide /
-                exp / rsqrt = 1) over the FP64 peak, or algorithmic HBM bytes
-                (8 + 8*33 per argument) over the measured copy bandwidth,
-                whichever roof takes longer.
+* ``roofline``  the dominant kernel (the FP64 evaluation kernel) against the
+                HBM roof: algorithmic bytes (8 + 8*33 per argument) over the
+                measured copy bandwidth; beside it the paper's algorithmic
+                FP64 flops (FMA = 2, each divide / exp / rsqrt = 1) over the
+                nominal FP64 peak, which the kernel can exceed because much
+                of that work runs on its integer pipes.
 * ``cpu_baseline`` the binary128 oracle on the host cores, on a bounded
                 sample of the same workload.
 ``--impl reference`` times that oracle alone (rank 0 only) and prints its line.
@@ -219,7 +220,7 @@ def oracle_sample_rate(kmax, seconds=12.0, threads=0, start=0):
     chunk = 2048
     done = 0
     t0 = time.perf_counter()
-    pool = W.mixture_c2(1 << 18, seed=1)
+    pool = W.mixture_c2(1 << 21, seed=1)
     while time.perf_counter() - t0 < seconds and done + chunk <= pool.size:
         oracle.boys(pool[done:done + chunk], kmax, nthreads=threads)
         done += chunk
@@ -328,22 +329,21 @@ def run_ours(args):
     avg_launch_s = statistics.mean(launch_ms) / 1e3
     bytes_per_launch = n * 8 * (KMAX + 2)
     flops_per_launch = n * fpx
-    t_hbm = bytes_per_launch / (hbm_gbs * 1e9)
-    t_fp64 = flops_per_launch / (FP64_PEAK_TFLOPS * 1e12)
-    if t_fp64 >= t_hbm:
-        roof = {"bound": "alu", "achieved": flops_per_launch / avg_launch_s / 1e12, "peak": FP64_PEAK_TFLOPS,
-                "unit": "TFLOP/s", "peak_source": fp64_peak_source}
-    else:
-        roof = {"bound": "hbm", "achieved": bytes_per_launch / avg_launch_s / 1e9, "peak": hbm_gbs,
-                "unit": "GB/s", "peak_source": f"{hbm_src} copy bandwidth"}
+    # Primary roof: HBM, the hard floor of stored mode (8 + 8*33 bytes per
+    # argument must move).  The paper's algorithmic FP64 work per argument is
+    # reported beside it: the kernel runs much of it (e^{-x}, the anchors'
+    # inverse square root, most recurrence steps) on the integer pipes, so
+    # that fraction can exceed 1 and does not bound the kernel.
+    roof = {"bound": "hbm", "achieved": bytes_per_launch / avg_launch_s / 1e9, "peak": hbm_gbs,
+            "unit": "GB/s", "peak_source": f"{hbm_src} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"}
     roof["frac"] = roof["achieved"] / roof["peak"]
     same_kernel = TRAFFIC_CAPTURE["sources_sha256"] == kernel_sources_sha256()
     roof["traffic"] = TRAFFIC_CAPTURE["bytes_per_x"] * n if same_kernel else None
     roof["kernel"] = "k_eval_f64<32>"
-    roof["algorithmic_flops_per_x"] = fpx
     roof["algorithmic_bytes_per_x"] = 8 * (KMAX + 2)
-    roof["hbm_frac"] = bytes_per_launch / avg_launch_s / 1e9 / hbm_gbs
-    roof["fp64_frac"] = flops_per_launch / avg_launch_s / 1e12 / FP64_PEAK_TFLOPS
+    roof["fp64_algorithmic"] = {"flops_per_x": fpx, "achieved": flops_per_launch / avg_launch_s / 1e12,
+                                "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "peak_source": fp64_peak_source,
+                                "frac": flops_per_launch / avg_launch_s / 1e12 / FP64_PEAK_TFLOPS}
 
     def time_launches(fn, reps):
         """Mean device time of one launch of fn on the stream, after warm-up."""
@@ -496,6 +496,14 @@ def run_ours(args):
         r1.record(stream)
         torch.cuda.synchronize(dev)
         rms = r0.elapsed_time(r1) / args.steps
+        # the same batch without a plan: boys_eval_ragged with a grouped-size
+        # workspace (device-built tile table, one launch per kmax)
+        wsb = _lib.lib().boys_ragged_workspace_size_grouped(int(km3.size), int(x3.size))
+        ws3 = torch.empty(wsb, dtype=torch.uint8, device=dev)
+        o3 = torch.empty_like(plan.out)
+        pl_ms = time_launches(lambda: pb.boys_eval_ragged(xt3, ot3, kt3, out=o3, out_off=plan.out_off, workspace=ws3),
+                              max(5, min(args.steps, 20)))
+        del ws3, o3
         lens = np.diff(off3)
         nval = int(np.sum((km3.astype(np.int64) + 1) * lens))
         rbytes = 8 * x3.size + 8 * nval + 20 * km3.size
@@ -504,6 +512,7 @@ def run_ours(args):
                   "segments": int(km3.size), "mean_kmax_weighted": float(np.sum(km3 * lens) / lens.sum()),
                   "hbm_gbs": rbytes / (rms / 1e3) / 1e9,
                   "fp64_frac": rfl / (rms / 1e3) / 1e12 / FP64_PEAK_TFLOPS, "config": plan.config(),
+                  "planless_ms": pl_ms, "planless_vs_plan": pl_ms / rms,
                   "launch": "one cudaGraphLaunch: workspace memset + " +
                             ("one kernel per kmax group (parallel graph branches)" if plan.config()["waves"] == 0
                              else "persistent kernel")}

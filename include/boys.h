@@ -136,18 +136,32 @@ boys_status boys_grad(const double* x, int64_t n, int kmax, const double* g, int
  *   out_off  [nseg]     int64 element offset of segment s's output block
  *   out                 F_k(x[seg_off[s] + j]) at out[out_off[s] + k*len_s + j],
  *                       len_s = seg_off[s+1] - seg_off[s]  (an order-major block)
- *   workspace           device scratch of boys_ragged_workspace_size() bytes,
- *                       16-byte aligned, owned by the caller; it holds the
- *                       persistent kernel's work counter (reset by a memset
- *                       enqueued before each launch) and an error word.  Calls
- *                       that share a workspace must not overlap on the GPU.
+ *   workspace           device scratch owned by the caller, 16-byte aligned, of
+ *                       workspace_bytes >= boys_ragged_workspace_size() (256);
+ *                       calls that share a workspace must not overlap on the GPU.
+ *                         * 256 bytes: one persistent launch over flat tiles,
+ *                           taking tiles from a work counter in the workspace;
+ *                         * boys_ragged_workspace_size_grouped(nseg, total)
+ *                           bytes (more than 528 in general): the kmax-grouped
+ *                           shape of a plan without a plan.  The call builds a
+ *                           table of tiles (up to 128 arguments of one segment)
+ *                           grouped by kmax in the workspace on the device,
+ *                           then launches one kernel per kmax.  If the table
+ *                           exceeds a smaller workspace (any size of at least
+ *                           528 bytes selects this shape), those kernels do
+ *                           nothing and a persistent launch runs instead.
+ *                       Either way everything is enqueued on `stream` with no
+ *                       synchronisation (about 38 launches for the grouped shape).
  * Every argument is evaluated by the same code as boys_eval at its segment's
- * kmax, so results are bitwise identical to per-segment boys_eval calls.
- * Descriptors live on the device and are not validated on the host; a
- * segment whose kmax is outside [0, 32] is skipped and flags the workspace
- * (see boys_ragged_status).
+ * kmax, so results are bitwise identical to per-segment boys_eval calls, for
+ * either shape.  Descriptors live on the device and are not validated on the
+ * host; a non-empty segment whose kmax is outside [0, 32] is skipped and
+ * flags the workspace (see boys_ragged_status).
  */
 size_t boys_ragged_workspace_size(void);
+/* Workspace bytes for the kmax-grouped shape of nseg segments holding `total`
+ * arguments in all (0 for negative arguments). */
+size_t boys_ragged_workspace_size_grouped(int32_t nseg, int64_t total);
 boys_status boys_eval_ragged(const double* x, const int64_t* seg_off, const int32_t* seg_kmax,
                              int32_t nseg, double* out, const int64_t* out_off, void* workspace,
                              size_t workspace_bytes, void* stream);

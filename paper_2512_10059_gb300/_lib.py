@@ -38,6 +38,7 @@ def _declare(lib):
         "boys_grad": (i32, [vp, i64, i32, vp, i64, vp, vp]),
         "boys_eval_f32": (i32, [vp, i64, i32, vp, i64, vp]),
         "boys_ragged_workspace_size": (ctypes.c_size_t, []),
+        "boys_ragged_workspace_size_grouped": (ctypes.c_size_t, [i32, i64]),
         "boys_eval_ragged": (i32, [vp, vp, vp, i32, vp, vp, vp, ctypes.c_size_t, vp]),
         "boys_ragged_status": (i32, [vp, ctypes.POINTER(i32), vp]),
         "boys_ragged_plan_create": (i32, [vp, vp, vp, i32, vp, vp, i32, ctypes.POINTER(vp)]),

@@ -205,9 +205,11 @@ def _ragged_args(x, seg_off, seg_kmax):
 
 
 def boys_eval_ragged(x, seg_off, seg_kmax, out=None, out_off=None, workspace=None, stream=None):
-    """All segments of a ragged batch in one persistent launch.  Returns
-    (out, out_off): segment s's F_k(x[seg_off[s]+j]) is at
-    out[out_off[s] + k*len_s + j]."""
+    """All segments of a ragged batch, without a plan.  Returns (out, out_off):
+    segment s's F_k(x[seg_off[s]+j]) is at out[out_off[s] + k*len_s + j].
+    Without ``workspace`` one of boys_ragged_workspace_size_grouped bytes is
+    allocated, which selects the kmax-grouped launches; a 256-byte workspace
+    selects the single persistent launch."""
     x, seg_off, seg_kmax = _ragged_args(x, seg_off, seg_kmax)
     nseg = seg_kmax.numel()
     if out_off is None:
@@ -221,7 +223,7 @@ def boys_eval_ragged(x, seg_off, seg_kmax, out=None, out_off=None, workspace=Non
         out = torch.empty(max(total_out, 1), dtype=torch.float64, device=x.device)
     _require(out, "out")
     L = _lib.lib()
-    wsb = L.boys_ragged_workspace_size()
+    wsb = L.boys_ragged_workspace_size_grouped(nseg, x.numel())
     if workspace is None:
         workspace = torch.empty(wsb, dtype=torch.uint8, device=x.device)
     st = L.boys_eval_ragged(x.data_ptr(), seg_off.data_ptr(), seg_kmax.data_ptr(), nseg, out.data_ptr(),

@@ -14,15 +14,16 @@
 #include "boys_internal.h"
 
 // Minimum resident blocks per SM of the stored-mode kernel, which caps its
-// registers: swept on GB300 with the FP64-step table of boys_fp64.cuh, 10
-// blocks (48 registers) up to kmax = 16 (8, 9 and 10 within 0.3% there) and 8
-// (64 registers) above (at kmax 24: 4.61 ms against 4.74 with 9 and 4.88
-// with 10).  BOYS_STORED_MIN_BLOCKS forces one value.
+// registers: swept on GB300 with the FP64-step table of boys_fp64.cuh, 12
+// blocks (40 registers) up to kmax = 7, 10 (48) up to 16 and 8 (64) above
+// (kmax 6: 2.16 ms with 12 against 2.19 with 10; kmax 8: 2.43 with 10
+// against 2.50 with 12; kmax 32: 5.30 with 8 against 5.45 with 9).
+// BOYS_STORED_MIN_BLOCKS forces one value.
 constexpr int stored_min_blocks(int kmax) {
 #ifdef BOYS_STORED_MIN_BLOCKS
     return BOYS_STORED_MIN_BLOCKS + 0 * kmax;
 #else
-    return kmax <= 16 ? 10 : 8;
+    return kmax <= 7 ? 12 : (kmax <= 16 ? 10 : 8);
 #endif
 }
 // FP64 recurrence steps and minimum resident blocks of the fused kernel.  Its

@@ -41,21 +41,21 @@ namespace fp64 {
 // (xf::exp_neg).  The set-up loads the FP64 pipe with the Horner sums only,
 // the same work at every kmax, while the integer pipes take one step per
 // order, so the balance depends on kmax only (the kernels are branch-free, so
-// not on the argument mix).  Swept on GB300 (stored mode, N = 2^26): every
-// step in FP64 up to kmax = 8, then 4 at 16, 8 at 24 and 12 or more at 32.
-// Defining BOYS_FP64_STEPS forces one value for every kmax.
-constexpr int kFp64Steps[33] = {0, 1, 2, 3, 4, 5, 6, 7, 8, 7, 7, 6, 6, 5, 5, 4, 4,
+// not on the argument mix).  Swept on GB300 (stored mode, N = 2^26, every
+// kmax 0..12 and every fourth above x 0..32 FP64 steps): none up to
+// kmax = 8, then floor((kmax - 7) / 2), 12 at kmax = 32 (5.30 ms, against
+// 6.73 with none and 5.46 with 14).  Defining BOYS_FP64_STEPS forces one
+// value for every kmax.
+constexpr int kFp64Steps[33] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 1, 1, 2, 2, 3, 3, 4, 4,
                                 5, 5, 6, 6, 7, 7, 8, 8, 9, 9, 10, 10, 11, 11, 12, 12};
 // Numerator and denominator of the anchor evaluated on the integer pipes
-// (xf::fma_i) instead of by FP64 FMAs, for kmax up to these limits (-1: never).
-// At small kmax the FP64 set-up binds while the integer pipes idle: moving
-// the denominator there took 28% off stored mode at kmax <= 2, 23% at 4, 8% at
-// 8, and added 9% at 12; moving the numerator as well overloads the integer
-// pipes at every kmax.  Ragged plans (one kernel per kmax) gain 3% with limit
-// 8 over limit 4; the persistent ragged kernel used without a plan, whose
-// warps run many per-kmax bodies at once, loses up to 6% (swept on GB300).
+// (xf::fma_i) instead of by FP64 FMAs, for kmax up to these limits (-1:
+// never).  With the rest of the set-up on the integer pipes the FP64 Horner
+// sums are cheaper at every kmax: at kmax 4, 2.07 ms with q in FP64 against
+// 2.71 with q on the integer pipes (best FP64-step count for each); at kmax
+// 32, 5.30 against 6.71.
 #ifndef BOYS_INT_HORNER_Q_MAXK
-#define BOYS_INT_HORNER_Q_MAXK 8
+#define BOYS_INT_HORNER_Q_MAXK -1
 #endif
 #ifndef BOYS_INT_HORNER_P_MAXK
 #define BOYS_INT_HORNER_P_MAXK -1

@@ -110,7 +110,9 @@ __global__ void __launch_bounds__(kMaxBlock, BOYS_RAGGED_MIN_BLOCKS) k_ragged(co
                                                       const int32_t* __restrict__ seg_kmax, int nseg,
                                                       double* __restrict__ out,
                                                       const int64_t* __restrict__ out_off,
-                                                      Workspace* __restrict__ ws) {
+                                                      Workspace* __restrict__ ws,
+                                                      const unsigned* __restrict__ gate) {
+    if (gate && *gate == 0) return;  // a fallback launch that is not needed
     __shared__ long long s_tile;
     __shared__ int s_seg_lo, s_seg_hi;
     const int64_t total = __ldg(seg_off + nseg);
@@ -191,19 +193,24 @@ static_assert(sizeof(Tile) == 16, "tile table entries are 16 bytes");
 
 constexpr int grouped_min_blocks(int kmax) { return kmax <= 16 ? 5 : 4; }  // 48 / 64 registers at 256 threads
 
+// One tile of a kmax group: its arguments, one per thread.
+template <int K>
+__device__ __forceinline__ void group_tile(const double* __restrict__ x, const int64_t* __restrict__ seg_off,
+                                           double* __restrict__ out, const int64_t* __restrict__ out_off,
+                                           const Tile& tl) {
+    if ((int)threadIdx.x < tl.len) {
+        const int64_t s0 = __ldg(seg_off + tl.seg);
+        const int64_t row = __ldg(seg_off + tl.seg + 1) - s0;
+        const int64_t j = tl.start + threadIdx.x;
+        fp64::eval_store<K>(__ldcs(x + s0 + j), out + __ldg(out_off + tl.seg) + j, row);
+    }
+}
+
 template <int K>
 __global__ void __launch_bounds__(kMaxBlock, grouped_min_blocks(K)) k_ragged_group(
         const double* __restrict__ x, const int64_t* __restrict__ seg_off, double* __restrict__ out,
         const int64_t* __restrict__ out_off, const Tile* __restrict__ tiles, int64_t ntiles) {
-    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
-        const Tile tl = tiles[t];
-        if ((int)threadIdx.x < tl.len) {
-            const int64_t s0 = __ldg(seg_off + tl.seg);
-            const int64_t row = __ldg(seg_off + tl.seg + 1) - s0;
-            const int64_t j = tl.start + threadIdx.x;
-            fp64::eval_store<K>(__ldcs(x + s0 + j), out + __ldg(out_off + tl.seg) + j, row);
-        }
-    }
+    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) group_tile<K>(x, seg_off, out, out_off, tiles[t]);
 }
 
 using GroupFn = void (*)(const double*, const int64_t*, double*, const int64_t*, const Tile*, int64_t);
@@ -213,7 +220,97 @@ constexpr auto group_table(std::integer_sequence<int, K...>) {
     return std::array<GroupFn, sizeof...(K)>{&k_ragged_group<K>...};
 }
 
-using KernelFn = void (*)(const double*, const int64_t*, const int32_t*, int, double*, const int64_t*, Workspace*);
+// ------------------------------------ kmax-grouped launches without a plan
+//
+// With a large enough workspace, boys_eval_ragged builds the kmax-grouped tile
+// table itself, on the device, at every call: a count of tiles per kmax, an
+// exclusive scan of the 33 counts, and a fill in which each segment takes a
+// contiguous range of its group with one atomic (the order of tiles inside a
+// group varies, the values do not).  Then one kernel per kmax reads its
+// group's range from the workspace.  If the table would exceed the
+// workspace's capacity, the group kernels return at once and a persistent
+// launch, gated on that condition, evaluates the batch instead.
+
+constexpr int kGroupTile = 128;  // arguments per tile = threads per block of the group kernels
+
+struct GroupHeader {
+    Workspace ws;             // error word (the persistent fallback also uses next_tile)
+    unsigned count[33];       // tiles per kmax
+    unsigned base[33];        // first tile of each group
+    unsigned cursor[33];      // fill positions
+    unsigned total;           // tiles in all
+    unsigned overflow;        // 1: the table does not fit, the persistent fallback runs
+};
+constexpr size_t kGroupHeaderBytes = 512;
+static_assert(sizeof(GroupHeader) <= kGroupHeaderBytes, "group header fits its reserved bytes");
+
+__device__ __forceinline__ bool bad_kmax(int k) { return k < 0 || k > 32; }
+
+__global__ void k_group_count(const int64_t* __restrict__ seg_off, const int32_t* __restrict__ seg_kmax, int nseg,
+                              GroupHeader* __restrict__ h) {
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < nseg; s += gridDim.x * blockDim.x) {
+        const int64_t len = __ldg(seg_off + s + 1) - __ldg(seg_off + s);
+        const int k = __ldg(seg_kmax + s);
+        if (len <= 0) continue;
+        if (bad_kmax(k)) {
+            atomicOr(&h->ws.error, 1ULL);
+            continue;
+        }
+        atomicAdd(&h->count[k], (unsigned)((len + kGroupTile - 1) / kGroupTile));
+    }
+}
+
+__global__ void k_group_scan(GroupHeader* __restrict__ h, unsigned long long capacity) {
+    if (threadIdx.x != 0) return;
+    unsigned long long run = 0;
+    for (int k = 0; k <= 32; ++k) {
+        h->base[k] = (unsigned)run;
+        h->cursor[k] = (unsigned)run;
+        run += h->count[k];
+    }
+    h->total = (unsigned)run;
+    h->overflow = run > capacity ? 1u : 0u;
+}
+
+__global__ void k_group_fill(const int64_t* __restrict__ seg_off, const int32_t* __restrict__ seg_kmax, int nseg,
+                             GroupHeader* __restrict__ h, Tile* __restrict__ tiles) {
+    if (h->overflow) return;
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < nseg; s += gridDim.x * blockDim.x) {
+        const int64_t len = __ldg(seg_off + s + 1) - __ldg(seg_off + s);
+        const int k = __ldg(seg_kmax + s);
+        if (len <= 0 || bad_kmax(k)) continue;
+        const unsigned n = (unsigned)((len + kGroupTile - 1) / kGroupTile);
+        const unsigned p = atomicAdd(&h->cursor[k], n);
+        for (unsigned t = 0; t < n; ++t) {
+            const int64_t a = (int64_t)t * kGroupTile;
+            tiles[p + t] = Tile{s, (int32_t)min((int64_t)kGroupTile, len - a), a};
+        }
+    }
+}
+
+template <int K>
+__global__ void __launch_bounds__(kGroupTile, 2 * grouped_min_blocks(K)) k_ragged_group_dev(
+        const double* __restrict__ x, const int64_t* __restrict__ seg_off, double* __restrict__ out,
+        const int64_t* __restrict__ out_off, const Tile* __restrict__ tiles, const GroupHeader* __restrict__ h) {
+    // The groups write disjoint outputs and read only the finished table, so
+    // the next kmax's kernel may start at once (programmatic dependent launch):
+    // its blocks take the SMs as this kernel's blocks retire, with no drain.
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    if (h->overflow) return;
+    const unsigned n = h->count[K];
+    const Tile* __restrict__ g = tiles + h->base[K];
+    for (unsigned t = blockIdx.x; t < n; t += gridDim.x) group_tile<K>(x, seg_off, out, out_off, g[t]);
+}
+
+using GroupDevFn = void (*)(const double*, const int64_t*, double*, const int64_t*, const Tile*, const GroupHeader*);
+
+template <int... K>
+constexpr auto group_dev_table(std::integer_sequence<int, K...>) {
+    return std::array<GroupDevFn, sizeof...(K)>{&k_ragged_group_dev<K>...};
+}
+
+using KernelFn = void (*)(const double*, const int64_t*, const int32_t*, int, double*, const int64_t*, Workspace*,
+                          const unsigned*);
 
 inline KernelFn kernel_for(int xpt) { return xpt == 2 ? &k_ragged<2> : &k_ragged<1>; }
 
@@ -243,8 +340,51 @@ boys_status launch(const Config& c, const double* x, const int64_t* seg_off, con
                    double* out, const int64_t* out_off, Workspace* ws, cudaStream_t stream) {
     boys_status st = check_cuda(cudaMemsetAsync(ws, 0, sizeof(Workspace), stream), "ragged workspace reset");
     if (st != BOYS_OK) return st;
-    kernel_for(c.xpt)<<<grid_size(c), c.block, 0, stream>>>(x, seg_off, seg_kmax, nseg, out, out_off, ws);
+    kernel_for(c.xpt)<<<grid_size(c), c.block, 0, stream>>>(x, seg_off, seg_kmax, nseg, out, out_off, ws, nullptr);
     return check_cuda(cudaGetLastError(), "ragged launch");
+}
+
+// The plan-less kmax-grouped batch on a workspace of `bytes` >= kGroupHeaderBytes
+// + 16: reset the header, build the table on the device, one launch per kmax,
+// then the persistent kernel gated on the table's overflow flag.
+boys_status launch_grouped(const double* x, const int64_t* seg_off, const int32_t* seg_kmax, int32_t nseg, double* out,
+                           const int64_t* out_off, void* workspace, size_t bytes, cudaStream_t stream) {
+    GroupHeader* h = (GroupHeader*)workspace;
+    Tile* tiles = (Tile*)((char*)workspace + kGroupHeaderBytes);
+    const unsigned long long capacity = std::min<unsigned long long>((bytes - kGroupHeaderBytes) / sizeof(Tile),
+                                                                     0xFFFFFFFFull);  // tile indices are 32-bit
+    boys_status st = check_cuda(cudaMemsetAsync(h, 0, sizeof(GroupHeader), stream), "ragged group header reset");
+    if (st != BOYS_OK) return st;
+    const int sgrid = (int)std::min<int64_t>((nseg + 255) / 256, (int64_t)sm_count() * 4);
+    k_group_count<<<sgrid, 256, 0, stream>>>(seg_off, seg_kmax, nseg, h);
+    k_group_scan<<<1, 32, 0, stream>>>(h, capacity);
+    k_group_fill<<<sgrid, 256, 0, stream>>>(seg_off, seg_kmax, nseg, h, tiles);
+    st = check_cuda(cudaGetLastError(), "ragged group table");
+    // One kernel per kmax, each launched as a programmatic dependent of the
+    // previous launch: a group kernel signals its dependents as it starts, and
+    // the fill kernel never does, so every group still starts after the table
+    // is complete.
+    static constexpr auto tg = group_dev_table(std::make_integer_sequence<int, 33>{});
+    cudaLaunchAttribute attr;
+    attr.id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr.val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t lc = {};
+    lc.blockDim = dim3(kGroupTile);
+    lc.stream = stream;
+    lc.attrs = &attr;
+    lc.numAttrs = 1;
+    for (int k = 0; k <= 32 && st == BOYS_OK; ++k) {
+        lc.gridDim = dim3(sm_count() * blocks_per_sm((const void*)tg[k], kGroupTile));
+        st = check_cuda(cudaLaunchKernelEx(&lc, tg[k], x, seg_off, out, out_off, (const Tile*)tiles,
+                                           (const GroupHeader*)h), "ragged group launch");
+    }
+    if (st != BOYS_OK) return st;
+    const Config c;
+    lc.gridDim = dim3(grid_size(c));
+    lc.blockDim = dim3(c.block);
+    return check_cuda(cudaLaunchKernelEx(&lc, kernel_for(c.xpt), x, seg_off, seg_kmax, (int)nseg, out, out_off,
+                                         &h->ws, (const unsigned*)&h->overflow),
+                      "ragged fallback launch");
 }
 
 // ------------------------------------------------------------- autotuning
@@ -350,6 +490,12 @@ struct boys_ragged_plan {
 
 BOYS_API size_t boys_ragged_workspace_size(void) { return 256; }
 
+BOYS_API size_t boys_ragged_workspace_size_grouped(int32_t nseg, int64_t total) {
+    if (nseg < 0 || total < 0) return 0;
+    // every segment of len arguments takes ceil(len / 128) <= len / 128 + 1 tiles
+    return ragged::kGroupHeaderBytes + sizeof(ragged::Tile) * ((size_t)total / ragged::kGroupTile + (size_t)nseg + 1);
+}
+
 BOYS_API boys_status boys_eval_ragged(const double* x, const int64_t* seg_off, const int32_t* seg_kmax,
                                       int32_t nseg, double* out, const int64_t* out_off, void* workspace,
                                       size_t workspace_bytes, void* stream) {
@@ -360,6 +506,9 @@ BOYS_API boys_status boys_eval_ragged(const double* x, const int64_t* seg_off, c
         return fail(BOYS_ERR_INVALID_ARG, "boys_eval_ragged: workspace_bytes=%zu < %zu", workspace_bytes,
                     boys_ragged_workspace_size());
     if (!aligned(workspace, 16)) return fail(BOYS_ERR_ALIGNMENT, "boys_eval_ragged: workspace not 16-byte aligned");
+    if (workspace_bytes >= ragged::kGroupHeaderBytes + sizeof(ragged::Tile))
+        return ragged::launch_grouped(x, seg_off, seg_kmax, nseg, out, out_off, workspace, workspace_bytes,
+                                      (cudaStream_t)stream);
     ragged::Config c;
     return ragged::launch(c, x, seg_off, seg_kmax, nseg, out, out_off, (ragged::Workspace*)workspace,
                           (cudaStream_t)stream);
@@ -679,7 +828,8 @@ BOYS_API boys_status boys_eval_ragged_noalloc(const double* x, const int64_t* se
     // the array keeps the previous call's contents: the counter must restart at zero
     st = check_cuda(cudaMemsetAsync(scratch, 0, sizeof(ragged::Workspace), s), "boys_eval_ragged_noalloc: scratch reset");
     if (st != BOYS_OK) return st;
-    ragged::k_ragged<1><<<grid, 128, 0, s>>>(x, seg_off, seg_kmax, nseg, out, out_off, (ragged::Workspace*)scratch);
+    ragged::k_ragged<1><<<grid, 128, 0, s>>>(x, seg_off, seg_kmax, nseg, out, out_off, (ragged::Workspace*)scratch,
+                                             nullptr);
     return check_cuda(cudaGetLastError(), "boys_eval_ragged_noalloc launch");
 }
 

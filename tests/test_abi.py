@@ -70,6 +70,9 @@ def test_grad_argument_errors(L):
 def test_ragged_argument_errors(L):
     import ctypes
     assert L.boys_ragged_workspace_size() == 256
+    assert L.boys_ragged_workspace_size_grouped(-1, 0) == 0
+    assert L.boys_ragged_workspace_size_grouped(0, 0) == 528
+    assert L.boys_ragged_workspace_size_grouped(4096, 1 << 25) == 512 + 16 * ((1 << 25) // 128 + 4097)
     assert L.boys_eval_ragged(FAKE, FAKE, FAKE, -1, FAKE, FAKE, FAKE, 256, None) == 1
     assert L.boys_eval_ragged(None, None, None, 0, None, None, None, 0, None) == 0
     assert L.boys_eval_ragged(FAKE, None, FAKE, 3, FAKE, FAKE, FAKE, 256, None) == 1

@@ -1,4 +1,6 @@
-"""Ragged batches (one persistent launch, per-segment kmax) through the C ABI.
+"""Ragged batches (per-segment kmax) through the C ABI: the plan-less call in
+both of its launch shapes (one persistent launch, or the kmax-grouped
+launches over a tile table it builds on the device) and the plans.
 
 Each argument must be evaluated by the same code as boys_eval at its
 segment's kmax: ragged and flat results are compared bitwise, across every
@@ -99,6 +101,45 @@ def test_graph_replay_and_workspace_reset():
     plan.close()
 
 
+def _workspace(nbytes):
+    return torch.empty(nbytes, dtype=torch.uint8, device=DEV)
+
+
+def test_planless_shapes_bitwise_identical():
+    """The grouped shape (default workspace), the persistent shape (256 bytes)
+    and the grouped shape whose table does not fit (528 + 16 bytes: the
+    persistent fallback runs) give the same bits."""
+    x, off, kmax = _small_batch(seed=11, nseg=250)
+    xt, ot, kt = _to(DEV, x, off, kmax)
+    grouped, out_off = pb.boys_eval_ragged(xt, ot, kt)
+    persistent, _ = pb.boys_eval_ragged(xt, ot, kt, workspace=_workspace(256))
+    overflow, _ = pb.boys_eval_ragged(xt, ot, kt, workspace=_workspace(528 + 16))
+    torch.cuda.synchronize()
+    assert torch.equal(grouped, persistent)
+    assert torch.equal(grouped, overflow)
+    _flat_reference(x, off, kmax, grouped, out_off)
+
+
+def test_grouped_bad_kmax_is_flagged_and_skipped():
+    x, off, kmax = _small_batch(seed=12, nseg=40)
+    lens = np.diff(off)
+    bad = int(np.flatnonzero(lens > 0)[2])
+    kmax[bad] = 33
+    xt, ot, kt = _to(DEV, x, off, kmax)
+    ws = _workspace(pb._lib.lib().boys_ragged_workspace_size_grouped(kmax.size, x.size))
+    out_off, total = pb.api.ragged_layout(ot, torch.from_numpy(np.minimum(kmax, 32)).to(DEV))
+    out = torch.full((total,), float("nan"), dtype=torch.float64, device=DEV)
+    pb.boys_eval_ragged(xt, ot, kt, out=out, out_off=out_off, workspace=ws)
+    assert pb.ragged_status(ws) is True
+    host = out.cpu().numpy()
+    oo = out_off.cpu().numpy()
+    assert np.isnan(host[oo[bad]:oo[bad] + 33 * lens[bad]]).all()
+    good = np.ones(kmax.size, bool)
+    good[bad] = False
+    for s in np.flatnonzero(good & (lens > 0)):
+        assert not np.isnan(host[oo[s]:oo[s] + (kmax[s] + 1) * lens[s]]).any()
+
+
 def test_bad_kmax_is_flagged_not_fatal():
     x, off, kmax = _small_batch(seed=9, nseg=20)
     kmax[5] = 40
@@ -128,6 +169,10 @@ def test_c3_full_batch_autotuned(tmp_path, monkeypatch):
     assert open(os.path.join(tmp_path, "tune.txt")).read().strip()
     plan2 = pb.RaggedPlan(xt, ot, kt, autotune=True)
     assert plan2.config() == plan.config()
+    # the plan-less call (grouped shape, device-built table) gives the same bits
+    planless, _ = pb.boys_eval_ragged(xt, ot, kt, out_off=plan.out_off, out=torch.empty_like(out))
+    torch.cuda.synchronize()
+    assert torch.equal(planless, out)
     rng = np.random.default_rng(3)
     segs = rng.choice(kmax.size, size=64, replace=False)
     oo = plan.out_off.cpu().numpy()
