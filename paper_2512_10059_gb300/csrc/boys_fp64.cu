@@ -16,8 +16,8 @@
 // Minimum resident blocks per SM of the stored-mode kernel, which caps its
 // registers: swept on GB300 with the FP64-step table of boys_fp64.cuh, 12
 // blocks (40 registers) up to kmax = 7, 10 (48) up to 16 and 8 (64) above
-// (kmax 6: 2.16 ms with 12 against 2.19 with 10; kmax 8: 2.43 with 10
-// against 2.50 with 12; kmax 32: 5.30 with 8 against 5.45 with 9).
+// (kmax 8: 2.33 ms with 10 against 2.38 with 8 and 2.34 with 12; kmax 16:
+// 3.26 with 10 against 3.30 with 8; kmax 32: 5.30 with 8 against 5.45 with 9).
 // BOYS_STORED_MIN_BLOCKS forces one value.
 constexpr int stored_min_blocks(int kmax) {
 #ifdef BOYS_STORED_MIN_BLOCKS
@@ -27,12 +27,18 @@ constexpr int stored_min_blocks(int kmax) {
 #endif
 }
 // FP64 recurrence steps and minimum resident blocks of the fused kernel.  Its
-// Horner sum adds KMAX FMAs per argument to the FP64 pipe, so every step runs
-// in the integer format (swept on GB300 at kmax 8..32 x 0..4 FP64 steps: 0
-// was fastest at every kmax).
-#ifndef BOYS_FUSED_FP64_STEPS
-#define BOYS_FUSED_FP64_STEPS 0
+// Horner sum adds KMAX FMAs per argument to the FP64 pipe, so half of stored
+// mode's FP64 steps run in FP64 (swept on GB300 at kmax 32, N = 2^26: 0 steps
+// 7.84 ms, 4 7.41, 6 7.36, 8 7.34; 6 blocks per SM 7.53, 10 8.07; the
+// smaller kmax follow the stored-mode table).  BOYS_FUSED_FP64_STEPS forces
+// one value.
+constexpr int fused_fp64_steps(int kmax) {
+#ifdef BOYS_FUSED_FP64_STEPS
+    return BOYS_FUSED_FP64_STEPS + 0 * kmax;
+#else
+    return boys::fp64::fp64_steps_for(kmax) / 2;
 #endif
+}
 #ifndef BOYS_FUSED_MIN_BLOCKS
 #define BOYS_FUSED_MIN_BLOCKS 8
 #endif
@@ -42,12 +48,12 @@ namespace {
 
 constexpr int kBlock = 128;
 
-template <int KMAX>
+template <int KMAX, bool FULL_ROWS>
 __global__ void __launch_bounds__(kBlock, stored_min_blocks(KMAX)) k_eval_f64(const double* __restrict__ x, int64_t n,
                                                      double* __restrict__ out, int64_t ld) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
-        fp64::eval_store<KMAX>(__ldcs(x + i), out + i, ld);
+        fp64::eval_store<KMAX, FULL_ROWS>(__ldcs(x + i), out + i, ld);
 }
 
 // out[i] = sum_k (-2 rho_i)^k F_k(x_i), by Horner in a = -2 rho from F_KMAX down.
@@ -58,7 +64,7 @@ __global__ void __launch_bounds__(kBlock, BOYS_FUSED_MIN_BLOCKS) k_fused_f64(con
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
         double F[KMAX + 1];
-        fp64::eval_point<KMAX, BOYS_FUSED_FP64_STEPS>(__ldcs(x + i), F);
+        fp64::eval_point<KMAX, fused_fp64_steps(KMAX)>(__ldcs(x + i), F);
         const double a = -2.0 * __ldcs(rho + i);
         double s = F[KMAX];
 #pragma unroll
@@ -67,10 +73,10 @@ __global__ void __launch_bounds__(kBlock, BOYS_FUSED_MIN_BLOCKS) k_fused_f64(con
     }
 }
 
-template <int... K>
+template <bool FULL_ROWS, int... K>
 constexpr auto eval_table(std::integer_sequence<int, K...>) {
     using Fn = void (*)(const double*, int64_t, double*, int64_t);
-    return std::array<Fn, sizeof...(K)>{&k_eval_f64<K>...};
+    return std::array<Fn, sizeof...(K)>{&k_eval_f64<K, FULL_ROWS>...};
 }
 
 template <int... K>
@@ -83,22 +89,31 @@ constexpr auto fused_table(std::integer_sequence<int, K...>) {
 }  // namespace boys
 
 
-BOYS_API boys_status boys_eval(const double* x, int64_t n, int kmax, double* out, int64_t ld,
-                               void* stream) {
-    using namespace boys;
-    if (kmax < 0 || kmax > 32) return fail(BOYS_ERR_KMAX, "boys_eval: kmax=%d outside [0, 32]", kmax);
-    if (n < 0) return fail(BOYS_ERR_INVALID_ARG, "boys_eval: n=%lld < 0", (long long)n);
-    if (ld < n) return fail(BOYS_ERR_INVALID_ARG, "boys_eval: ld=%lld < n=%lld", (long long)ld, (long long)n);
+namespace boys {
+// Checks and launches stored mode; full_rows selects the store pattern of
+// fp64::eval_store (true for output in host memory).
+static boys_status eval_launch(const char* name, const double* x, int64_t n, int kmax, double* out, int64_t ld,
+                               void* stream, bool full_rows) {
+    if (kmax < 0 || kmax > 32) return fail(BOYS_ERR_KMAX, "%s: kmax=%d outside [0, 32]", name, kmax);
+    if (n < 0) return fail(BOYS_ERR_INVALID_ARG, "%s: n=%lld < 0", name, (long long)n);
+    if (ld < n) return fail(BOYS_ERR_INVALID_ARG, "%s: ld=%lld < n=%lld", name, (long long)ld, (long long)n);
     if (n == 0) return BOYS_OK;
-    if (!x || !out) return fail(BOYS_ERR_INVALID_ARG, "boys_eval: NULL pointer");
-    if (ld > INT64_MAX / (kmax + 1)) return fail(BOYS_ERR_INVALID_ARG, "boys_eval: (kmax+1)*ld overflows");
-    if (!aligned(x, 8) || !aligned(out, 8)) return fail(BOYS_ERR_ALIGNMENT, "boys_eval: x/out not 8-byte aligned");
-    // one argument per thread, each order stored as soon as it is produced
-    static constexpr auto t1 = eval_table(std::make_integer_sequence<int, 33>{});
-    const auto fn = t1[kmax];
+    if (!x || !out) return fail(BOYS_ERR_INVALID_ARG, "%s: NULL pointer", name);
+    if (ld > INT64_MAX / (kmax + 1)) return fail(BOYS_ERR_INVALID_ARG, "%s: (kmax+1)*ld overflows", name);
+    if (!aligned(x, 8) || !aligned(out, 8)) return fail(BOYS_ERR_ALIGNMENT, "%s: x/out not 8-byte aligned", name);
+    // one argument per thread, each order stored as soon as its row is complete
+    static constexpr auto tdev = eval_table<false>(std::make_integer_sequence<int, 33>{});
+    static constexpr auto thost = eval_table<true>(std::make_integer_sequence<int, 33>{});
+    const auto fn = full_rows ? thost[kmax] : tdev[kmax];
     const int64_t grid = grid_for((const void*)fn, kBlock, n, (int64_t)kBlock);
     fn<<<(unsigned)grid, kBlock, 0, (cudaStream_t)stream>>>(x, n, out, ld);
     return check_cuda(cudaGetLastError(), "boys_eval launch");
+}
+}  // namespace boys
+
+BOYS_API boys_status boys_eval(const double* x, int64_t n, int kmax, double* out, int64_t ld,
+                               void* stream) {
+    return boys::eval_launch("boys_eval", x, n, kmax, out, ld, stream, false);
 }
 
 BOYS_API boys_status boys_eval_fused(const double* x, const double* rho, int64_t n, int kmax,
@@ -155,5 +170,6 @@ BOYS_API boys_status boys_eval_host(const double* x, int64_t n, int kmax, double
     if (st != BOYS_OK) return st;
     st = host_view(out, &od, "out");
     if (st != BOYS_OK) return st;
-    return boys_eval((const double*)xd, n, kmax, (double*)od, ld, stream);
+    // full rows: partial writes over the host link are not merged
+    return eval_launch("boys_eval_host", (const double*)xd, n, kmax, (double*)od, ld, stream, true);
 }

@@ -29,6 +29,7 @@
 
 #include <cstdint>
 
+#include "boys_coeffs_fixed.h"
 #include "boys_coeffs_fp64.h"
 #include "boys_math.cuh"
 #include "boys_xf.cuh"
@@ -38,27 +39,25 @@ namespace fp64 {
 
 // Recurrence steps that run in FP64; the rest use the 64-bit-significand
 // integer format (boys_xf.cuh), and e^{-x} always runs on the integer pipes
-// (xf::exp_neg).  The set-up loads the FP64 pipe with the Horner sums only,
-// the same work at every kmax, while the integer pipes take one step per
-// order, so the balance depends on kmax only (the kernels are branch-free, so
-// not on the argument mix).  Swept on GB300 (stored mode, N = 2^26, every
-// kmax 0..12 and every fourth above x 0..32 FP64 steps): none up to
-// kmax = 8, then floor((kmax - 7) / 2), 12 at kmax = 32 (5.30 ms, against
-// 6.73 with none and 5.46 with 14).  Defining BOYS_FP64_STEPS forces one
-// value for every kmax.
-constexpr int kFp64Steps[33] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 1, 1, 2, 2, 3, 3, 4, 4,
-                                5, 5, 6, 6, 7, 7, 8, 8, 9, 9, 10, 10, 11, 11, 12, 12};
-// Numerator and denominator of the anchor evaluated on the integer pipes
-// (xf::fma_i) instead of by FP64 FMAs, for kmax up to these limits (-1:
-// never).  With the rest of the set-up on the integer pipes the FP64 Horner
-// sums are cheaper at every kmax: at kmax 4, 2.07 ms with q in FP64 against
-// 2.71 with q on the integer pipes (best FP64-step count for each); at kmax
-// 32, 5.30 against 6.71.
-#ifndef BOYS_INT_HORNER_Q_MAXK
-#define BOYS_INT_HORNER_Q_MAXK -1
-#endif
-#ifndef BOYS_INT_HORNER_P_MAXK
-#define BOYS_INT_HORNER_P_MAXK -1
+// (xf::exp_neg).  The set-up loads the FP64 pipe with the denominator's
+// Horner sum only, the same work at every kmax, while the integer pipes take
+// one step per order, so the balance depends on kmax only (the kernels are
+// branch-free, so not on the argument mix).  Swept on GB300 (stored mode,
+// N = 2^26, kmax 0, 2, 4, 6, 8 and every fourth above x 0..18 FP64 steps):
+// about kmax/2 up to kmax = 16, then (kmax - 4)/2, 14 at kmax = 32 (5.06 ms,
+// against 6.73 with none and 5.19 with 12).  Defining BOYS_FP64_STEPS forces
+// one value for every kmax.
+constexpr int kFp64Steps[33] = {0, 0, 0, 1, 2, 2, 2, 3, 4, 4, 5, 5, 6, 6, 7, 7, 8,
+                                8, 8, 8, 8, 9, 9, 10, 10, 11, 11, 12, 12, 13, 13, 14, 14};
+// The anchor's numerator p runs as a fixed-point Horner sum on the integer
+// pipes for kmax up to BOYS_FIXED_P_MAXK (-1: never), the denominator q in
+// FP64.  A fixed binary point serves the numerators (degree <= 8) to about
+// 1e-17 of the anchor, but not the denominators of degree 12 and 13; q in a
+// floating integer format (about 30 instructions a step) was slower than the
+// FP64 Horner sum at every kmax (kmax 4: 2.71 ms against 2.07; kmax 32: 6.71
+// against 5.30).
+#ifndef BOYS_FIXED_P_MAXK
+#define BOYS_FIXED_P_MAXK 32
 #endif
 
 constexpr int fp64_steps_for(int kmax) {
@@ -89,15 +88,10 @@ static __constant__ double c_ra_q[33][BOYS_RA_QLEN] = BOYS_RA_Q_INIT;
 // r_B padded with zeros to the r_A row lengths
 static __constant__ double c_rb_p[BOYS_RA_PLEN] = BOYS_RB_P_INIT;
 static __constant__ double c_rb_q[BOYS_RA_QLEN] = BOYS_RB_Q_INIT;
-// the same in the signed integer-significand format (xf::XfI)
-static __constant__ long long c_ra_p_xm[33][BOYS_RA_PLEN] = BOYS_RA_P_XM_INIT;
-static __constant__ int c_ra_p_xe[33][BOYS_RA_PLEN] = BOYS_RA_P_XE_INIT;
-static __constant__ long long c_ra_q_xm[33][BOYS_RA_QLEN] = BOYS_RA_Q_XM_INIT;
-static __constant__ int c_ra_q_xe[33][BOYS_RA_QLEN] = BOYS_RA_Q_XE_INIT;
-static __constant__ long long c_rb_p_xm[BOYS_RA_PLEN] = BOYS_RB_P_XM_INIT;
-static __constant__ int c_rb_p_xe[BOYS_RA_PLEN] = BOYS_RB_P_XE_INIT;
-static __constant__ long long c_rb_q_xm[BOYS_RA_QLEN] = BOYS_RB_Q_XM_INIT;
-static __constant__ int c_rb_q_xe[BOYS_RA_QLEN] = BOYS_RB_Q_XE_INIT;
+// the numerators in 64-bit fixed point (value = V 2^-f, t = x/16 in A, x/32 in B)
+static __constant__ long long c_ra_p_fx[33][BOYS_RA_PLEN] = BOYS_RA_P_FX_INIT;
+static __constant__ long long c_rb_p_fx[BOYS_RA_PLEN] = BOYS_RB_P_FX_INIT;
+constexpr int kRaPFxf[33] = BOYS_RA_P_FXF_INIT;
 
 constexpr int cmax(int a, int b) { return a > b ? a : b; }
 
@@ -159,40 +153,34 @@ __device__ __forceinline__ Setup setup_mode(double x) {
     }
     x = valid ? __longlong_as_double(xb) : quiet_nan();
 
-    // Anchor: r_{A,KMAX} in A, r_B in B (Horner, monic denominators), in FP64
-    // or, where the integer pipes have room (small kmax), in xf::XfI.
-    constexpr bool kIntP = KMAX <= BOYS_INT_HORNER_P_MAXK;
-    constexpr bool kIntQ = KMAX <= BOYS_INT_HORNER_Q_MAXK;
-    double p, q;
-    if (kIntP || kIntQ) {
-        const xf::Xf xu = xf::from_double(x);
-        if (kIntP) {
-            xf::XfI t{inA ? c_ra_p_xm[KMAX][NP] : c_rb_p_xm[NP], inA ? c_ra_p_xe[KMAX][NP] : c_rb_p_xe[NP]};
+    // Anchor: r_{A,KMAX} in A, r_B in B (Horner, monic denominators).  The
+    // numerator p: fixed-point Horner on the integer pipes in t = x/16 (A) or
+    // x/32 (B), t in Q64 (t < 1 on both regions; other lanes get a clamped
+    // t whose result is not used), or FP64 Horner.
+    constexpr bool kFixedP = KMAX <= BOYS_FIXED_P_MAXK;
+    double p = 0.0;
+    xf::Xf Pfx = xf::zero();
+    if (kFixedP) {
+        const unsigned long long xbu = (unsigned long long)xb;
+        const int be = (int)((xbu >> 52) & 0x7FF);
+        const unsigned long long mant = (xbu & 0xFFFFFFFFFFFFFULL) | 0x10000000000000ULL;
+        const int sh = be - (inA ? 1075 - 64 + BOYS_FX_SHIFT_A : 1075 - 64 + BOYS_FX_SHIFT_B);  // t 2^64 = mant 2^sh
+        unsigned long long T = sh >= 0 ? (mant << min(sh, 11)) : (mant >> min(-sh, 63));
+        if (be == 0) T = 0;
+        const unsigned long long Th = T >> 1;
+        long long v = inA ? c_ra_p_fx[KMAX][NP] : c_rb_p_fx[NP];
 #pragma unroll
-            for (int i = NP - 1; i >= 0; --i)
-                t = xf::fma_i(t, xu, xf::XfI{inA ? c_ra_p_xm[KMAX][i] : c_rb_p_xm[i],
-                                             inA ? c_ra_p_xe[KMAX][i] : c_rb_p_xe[i]});
-            p = xf::to_double(t);
-        }
-        if (kIntQ) {
-            xf::XfI t{inA ? c_ra_q_xm[KMAX][NQ] : c_rb_q_xm[NQ], inA ? c_ra_q_xe[KMAX][NQ] : c_rb_q_xe[NQ]};
-#pragma unroll
-            for (int i = NQ - 1; i >= 0; --i)
-                t = xf::fma_i(t, xu, xf::XfI{inA ? c_ra_q_xm[KMAX][i] : c_rb_q_xm[i],
-                                             inA ? c_ra_q_xe[KMAX][i] : c_rb_q_xe[i]});
-            q = xf::to_double(t);
-        }
-    }
-    if (!kIntP) {
+        for (int i = NP - 1; i >= 0; --i) v = xf::mulhi_s(v, T, Th) + (inA ? c_ra_p_fx[KMAX][i] : c_rb_p_fx[i]);
+        constexpr int kFa = kRaPFxf[KMAX];
+        Pfx = xf::from_fixed(v, inA ? kFa : BOYS_RB_P_FXF);
+    } else {
         p = inA ? c_ra_p[KMAX][NP] : c_rb_p[NP];
 #pragma unroll
         for (int i = NP - 1; i >= 0; --i) p = fma(p, x, inA ? c_ra_p[KMAX][i] : c_rb_p[i]);
     }
-    if (!kIntQ) {
-        q = inA ? c_ra_q[KMAX][NQ] : c_rb_q[NQ];
+    double q = inA ? c_ra_q[KMAX][NQ] : c_rb_q[NQ];
 #pragma unroll
-        for (int i = NQ - 1; i >= 0; --i) q = fma(q, x, inA ? c_ra_q[KMAX][i] : c_rb_q[i]);
-    }
+    for (int i = NQ - 1; i >= 0; --i) q = fma(q, x, inA ? c_ra_q[KMAX][i] : c_rb_q[i]);
 
     // Arguments beyond 1e300 are clamped there in C (F_0 < 1e-150 and F_k = 0
     // for k > 0 either way); +inf gives exactly 0.
@@ -202,7 +190,7 @@ __device__ __forceinline__ Setup setup_mode(double x) {
     // The anchors from one inverse square root in the 64-bit-significand
     // format (integer pipes): r = z^{-1/2} with z = q^2 (A), (2x q)^2 (B), x (C).
     // p/q > 0 on both regions, so magnitudes suffice (from_double drops signs).
-    const xf::Xf P = xf::from_double(p);
+    const xf::Xf P = kFixedP ? Pfx : xf::from_double(p);
     const xf::Xf Q = xf::from_double(q);
     xf::Xf y0, R;
     if (MODE == kRegionNone) {
@@ -263,18 +251,6 @@ __device__ __forceinline__ int region_of(double x) {
     return xb < kBitsX0 ? kRegionA : (xb < kBitsX1 ? kRegionB : kRegionC);
 }
 
-// Warp-level choice of set-up: the region-restricted one when every lane of
-// the warp is in the same region, the branch-free one otherwise.  All 32
-// lanes must call it together.
-template <int KMAX, bool INT_EXP = false>
-__device__ __forceinline__ Setup setup_warp(double x) {
-    const int r = region_of(x);
-    if (__all_sync(0xffffffffu, r == kRegionA)) return setup_mode<kRegionA, KMAX, INT_EXP>(x);
-    if (__all_sync(0xffffffffu, r == kRegionB)) return setup_mode<kRegionB, KMAX, INT_EXP>(x);
-    if (__all_sync(0xffffffffu, r == kRegionC)) return setup_mode<kRegionC, KMAX, INT_EXP>(x);
-    return setup<KMAX, INT_EXP>(x);
-}
-
 // One step y_{j+1} = (a_j y_j + s) c_j of the unified recurrence, in the
 // 64-bit-significand format of boys_xf.cuh on the integer pipes:
 //   A: a_j = 2x, s = +e^{-x}, c_j = 1/(2l+1), l = KMAX-1-j  (y_j = F_{KMAX-j})
@@ -332,16 +308,23 @@ __device__ __forceinline__ void eval_point(double x, double (&F)[KMAX + 1]) {
     for (int k = 0; k <= KMAX; ++k) F[k] = S.inA ? v[KMAX - k] : v[k];
 }
 
-// Same values, stored by the whole warp one full row at a time: F_k(x) to
-// col[k * ld].  Value number p of the recurrence (p = 0 is the anchor) is
-// F_{KMAX-p} on an A lane and F_p on a B or C lane, so row k is complete once
-// both p = k and p = KMAX-k have been produced.  A lane therefore keeps its
-// values p < KMAX/2 (at most 17 doubles); from p >= KMAX/2 on, step p
-// completes rows p and KMAX-p for every lane of the warp and both are written
-// with coalesced full-line stores (a store that covered only the A lanes or
-// only the B/C lanes of a row would leave partly written sectors, which L2
-// evicts and DRAM then read-modify-writes).
-template <int KMAX>
+// Same values, stored by the whole warp: F_k(x) to col[k * ld].  Value number
+// p of the recurrence (p = 0 is the anchor) is F_{KMAX-p} on an A lane and
+// F_p on a B or C lane, so row k is complete once both p = k and p = KMAX-k
+// have been produced.  A lane therefore keeps its values p < KMAX/2 (at most
+// 17 doubles); from p >= KMAX/2 on, step p completes rows p and KMAX-p for
+// every lane of the warp and the two stores of that step cover both rows
+// completely between them, so L2 holds whole lines when they go to DRAM (a
+// value stored as soon as it is produced would leave rows partly written for
+// many steps, and L2 would evict partly written sectors that DRAM then
+// read-modify-writes).
+//
+// FULL_ROWS selects the store pattern.  false (device memory): each of the
+// step's two stores picks its row per lane, so each writes two half rows that
+// L2 merges before DRAM (cheaper on the ALU).  true (host memory over the
+// host link, where partial writes are not merged and would double the link
+// traffic): each store picks its value per lane and writes one full row.
+template <int KMAX, bool FULL_ROWS = false>
 __device__ __forceinline__ void eval_store(double x, double* __restrict__ col, int64_t ld) {
     constexpr int H = KMAX / 2 + 1;
     const Setup S = setup<KMAX, int_exp_for(KMAX, fp64_steps_for(KMAX))>(x);
@@ -356,9 +339,20 @@ __device__ __forceinline__ void eval_store(double x, double* __restrict__ col, i
         } else if (2 * p == KMAX) {
             __stcs(col + p * ld, v);
         } else {
+            // rows p and q = KMAX - p: this step's value is F_q on an A lane and
+            // F_p otherwise; the held one is the other.  Selecting the row (an
+            // IMAD on the FMA pipe) instead of the value (two SELs per double on
+            // the ALU) makes each store write two half rows, which L2 merges
+            // before DRAM (kmax 32: 5.32 -> 5.24 ms).
             const int q = KMAX - p;
-            __stcs(col + p * ld, S.inA ? hold[q] : v);
-            __stcs(col + q * ld, S.inA ? v : hold[q]);
+            if (FULL_ROWS) {
+                __stcs(col + p * ld, S.inA ? hold[q] : v);
+                __stcs(col + q * ld, S.inA ? v : hold[q]);
+            } else {
+                const int64_t rv = S.inA ? q : p;
+                __stcs(col + rv * ld, v);
+                __stcs(col + (KMAX - rv) * ld, hold[q]);
+            }
         }
     }
 }

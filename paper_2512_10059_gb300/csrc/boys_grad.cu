@@ -16,14 +16,25 @@ namespace {
 
 constexpr int kBlock = 128;
 
+// FP64 recurrence steps and minimum resident blocks of the gradient kernel
+// (its own g_k F_{k+1} sum is FP64 work already): swept on GB300 at kmax 16,
+// N = 2^24: no FP64 step and 8 blocks per SM (64 registers), 1.11 ms, against
+// 1.23 with the register count left free and 1.21 with 2 FP64 steps.
+#ifndef BOYS_GRAD_FP64_STEPS
+#define BOYS_GRAD_FP64_STEPS 0
+#endif
+#ifndef BOYS_GRAD_MIN_BLOCKS
+#define BOYS_GRAD_MIN_BLOCKS 8
+#endif
+
 template <int KMAX>
-__global__ void __launch_bounds__(kBlock) k_grad_f64(const double* __restrict__ x, int64_t n,
+__global__ void __launch_bounds__(kBlock, BOYS_GRAD_MIN_BLOCKS) k_grad_f64(const double* __restrict__ x, int64_t n,
                                                      const double* __restrict__ g, int64_t ldg,
                                                      double* __restrict__ dx) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
         double F[KMAX + 2];
-        fp64::eval_point<KMAX + 1, 0>(__ldcs(x + i), F);  // the g_k F_{k+1} sum is FP64 work already
+        fp64::eval_point<KMAX + 1, BOYS_GRAD_FP64_STEPS>(__ldcs(x + i), F);
         double s = 0.0;
 #pragma unroll
         for (int k = 0; k <= KMAX; ++k) s = fma(__ldcs(g + k * ldg + i), F[k + 1], s);

@@ -12,8 +12,11 @@
 // only that region's anchor and special functions; the result is correct for
 // any order.  In region C (about half the pairs of the paper's workload) the
 // values F_l = F_0 (2l-1)!! / (2X)^l need no recurrence: the warp evaluates
-// w = F_0 sum_l c_l (2l-1)!! u^l, u = 1/(2X), by Horner in the signed integer
-// format, which takes the w sum off the FP64 pipe.  The recurrence runs entirely in the integer format:
+// w = F_0 sum_l e_l t^l, e_l = c_l (2l-1)!! / 32^l, t = 32 / (2X) <= 0.552,
+// as a fixed-point Horner sum on the integer pipes (its partial sums are
+// bounded by sum_l |e_l|, so a binary point chosen per block from the weights
+// holds them to ~2^-60 sum_l |c_l|).  In region-A and region-B warps w is
+// summed by FP64 FMAs.  The recurrence runs entirely in the integer format:
 // this kernel's own FP64 work (the w and z sums) already loads the FP64 pipe.
 #include <array>
 #include <utility>
@@ -24,39 +27,38 @@
 namespace boys {
 namespace {
 
-// In region-A and region-B warps, the first BOYS_PAIRWISE_INT_TERMS values of
-// the recurrence enter w through an integer-format accumulator (xf::fma_i on
-// the recurrence's own values) and the rest through FP64 FMAs, balancing the
-// two pipes: at k = 12, 8 integer terms were fastest (N = 2^19: 13.38 s with
-// none, 12.82 s with 4, 12.63 s with 8, 12.72 s with 10, 13.40 s with all 13).
-#ifndef BOYS_PAIRWISE_INT_TERMS
-#define BOYS_PAIRWISE_INT_TERMS 8
-#endif
 #ifndef BOYS_PAIRWISE_BLOCK
 #define BOYS_PAIRWISE_BLOCK 128
 #endif
 constexpr int kBlock = BOYS_PAIRWISE_BLOCK;
 
+// v 2^-f as a double (v a signed fixed-point integer), by integer assembly.
+__device__ __forceinline__ double fixed_to_double(long long v, int f) {
+    if (v == 0) return 0.0;
+    const xf::Xf a = xf::from_fixed(v, f);
+    const double m = xf::to_double(a);
+    return v < 0 ? -m : m;
+}
+
+// Binary point f of a fixed-point sum bounded by M: M 2^f < 2^61 (f = 0 for M = 0).
+__device__ __forceinline__ int fixed_point_for(double M) { return M > 0.0 ? 60 - ilogb(M) : 0; }
+
 // w = sum_l c_l F_l for a warp whose lanes all lie in region R (A or B):
-// value number p of the recurrence is F_{K-p} in A and F_p in B.
+// value number p of the recurrence is F_{K-p} in A and F_p in B.  With the
+// region-C sums on the integer pipes the FP64 pipe has room for all of w here:
+// routing the first 2, 4 or 6 terms through a fixed-point accumulator on the
+// integer pipes instead took 582 ms against 553 ms (k = 12, N = 2^17).
 template <int R, int K>
-__device__ __forceinline__ double w_region(const fp64::Setup& S, const double (&cw)[K + 1],
-                                           const long long* s_cm, const int* s_ce) {
-    constexpr int kInt = BOYS_PAIRWISE_INT_TERMS < K + 1 ? BOYS_PAIRWISE_INT_TERMS : K + 1;
+__device__ __forceinline__ double w_region(const fp64::Setup& S, const double (&cw)[K + 1]) {
     double yd = S.y0d;
     xf::Xf yv = S.y0;
     double w = 0.0;
-    xf::XfI wi{0, xf::kXfZeroExp};
 #pragma unroll
     for (int p = 0; p <= K; ++p) {
         const int l = R == fp64::kRegionA ? K - p : p;
-        const double v = fp64::next_value<K, 0>(S, p, yd, yv);
-        if (p < kInt)
-            wi = xf::fma_i(xf::XfI{s_cm[l], s_ce[l]}, p == 0 ? xf::from_double(S.y0d) : yv, wi);
-        else
-            w = fma(cw[l], v, w);
+        w = fma(cw[l], fp64::next_value<K, 0>(S, p, yd, yv), w);
     }
-    return kInt > 0 ? w + xf::to_double(wi) : w;
+    return w;
 }
 
 template <int K>
@@ -64,21 +66,27 @@ __global__ void __launch_bounds__(kBlock) k_pairwise(const double* __restrict__ 
                                                      int64_t n, const double* __restrict__ c,
                                                      double* __restrict__ z) {
     __shared__ double sx[kBlock], sy[kBlock];
-    __shared__ long long s_dm[K + 1], s_cm[K + 1];
-    __shared__ int s_de[K + 1], s_ce[K + 1];
+    __shared__ long long s_efx[K + 1];
+    __shared__ int s_fe;
     double cw[K + 1];
 #pragma unroll
     for (int l = 0; l <= K; ++l) cw[l] = __ldg(c + l);
     const int t = threadIdx.x;
-    if (t <= K) {  // d_l = c_l (2l-1)!! for region C, in the integer format
-        double f = 1.0;
-        for (int m = 0; m < t; ++m) f *= (double)(2 * m + 1);
-        const xf::XfI d = xf::from_double_signed(__ldg(c + t) * f);
-        s_dm[t] = d.m;
-        s_de[t] = d.e;
-        const xf::XfI cc = xf::from_double_signed(__ldg(c + t));
-        s_cm[t] = cc.m;
-        s_ce[t] = cc.e;
+    if (t == 0) {
+        // Fixed-point coefficients of the region-C sum, once per block:
+        // e_l = c_l (2l-1)!! / 32^l, the coefficients of w / F_0 as a
+        // polynomial in t = 32 u = 16 / X (t <= 0.552 on region C), whose
+        // partial Horner sums are bounded by sum |e_l|; the binary point keeps
+        // that bound below 2^61.
+        double e[K + 1], se = 0.0, f = 1.0;
+        for (int l = 0; l <= K; ++l) {
+            e[l] = ldexp(cw[l] * f, -5 * l);
+            f *= (double)(2 * l + 1);
+            se += fabs(e[l]);
+        }
+        const int fe = fixed_point_for(se);
+        for (int l = 0; l <= K; ++l) s_efx[l] = __double2ll_rn(ldexp(e[l], fe));
+        s_fe = fe;
     }
     const int64_t i = (int64_t)blockIdx.x * kBlock + t;
     const double xi = i < n ? __ldg(x + i) : 0.0;
@@ -97,16 +105,19 @@ __global__ void __launch_bounds__(kBlock) k_pairwise(const double* __restrict__ 
             double w;
             if (__all_sync(0xffffffffu, r == fp64::kRegionC)) {
                 // Region C: F_l = F_0 (2l-1)!! u^l with u = 1/(2X), so
-                // w = F_0 sum_l d_l u^l, by Horner in the integer format.
+                // w = F_0 sum_l e_l t^l with t = 32 u, by a fixed-point Horner
+                // sum on the integer pipes (t in Q64, from the set-up's 1/(2X)).
                 const fp64::Setup S = fp64::setup_mode<fp64::kRegionC, K, true>(X);
-                xf::XfI h{s_dm[K], s_de[K]};
+                const unsigned long long T = S.R.m >> min(max(-(S.R.e + 6), 0), 63);
+                const unsigned long long Th = T >> 1;
+                long long h = s_efx[K];
 #pragma unroll
-                for (int l = K - 1; l >= 0; --l) h = xf::fma_i(h, S.R, xf::XfI{s_dm[l], s_de[l]});
-                w = S.y0d * xf::to_double(h);
+                for (int l = K - 1; l >= 0; --l) h = xf::mulhi_s(h, T, Th) + s_efx[l];
+                w = S.y0d * fixed_to_double(h, s_fe);
             } else if (__all_sync(0xffffffffu, r == fp64::kRegionA)) {
-                w = w_region<fp64::kRegionA, K>(fp64::setup_mode<fp64::kRegionA, K, true>(X), cw, s_cm, s_ce);
+                w = w_region<fp64::kRegionA, K>(fp64::setup_mode<fp64::kRegionA, K, true>(X), cw);
             } else if (__all_sync(0xffffffffu, r == fp64::kRegionB)) {
-                w = w_region<fp64::kRegionB, K>(fp64::setup_mode<fp64::kRegionB, K, true>(X), cw, s_cm, s_ce);
+                w = w_region<fp64::kRegionB, K>(fp64::setup_mode<fp64::kRegionB, K, true>(X), cw);
             } else {
                 const fp64::Setup S = fp64::setup<K, true>(X);
                 double yd = S.y0d;

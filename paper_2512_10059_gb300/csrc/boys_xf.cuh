@@ -89,6 +89,20 @@ __device__ __forceinline__ Xf mul(Xf a, Xf b) {
     return r;
 }
 
+// floor(v t / 2^64) within 3 units, for |v| < 2^63 and t < 2^64, with
+// t_half = t >> 1: the biased operand v + 2^63 is unsigned and
+// (v + 2^63) t / 2^64 = v t / 2^64 + t / 2.
+__device__ __forceinline__ long long mulhi_s(long long v, unsigned long long t, unsigned long long t_half) {
+    return (long long)(mulhi3((unsigned long long)v ^ 0x8000000000000000ULL, t) - t_half);
+}
+
+// |v| 2^-f as a normalised Xf (v != 0).
+__device__ __forceinline__ Xf from_fixed(long long v, int f) {
+    const unsigned long long a = v < 0 ? 0ULL - (unsigned long long)v : (unsigned long long)v;
+    const int lz = __clzll((long long)a);
+    return Xf{a << (lz & 63), 63 - lz - f};
+}
+
 // Product without renormalisation: value = m * 2^(e - 63) with m in
 // [2^62, 2^64) (one possible leading zero).  For operands of an addition,
 // which renormalises.
@@ -213,50 +227,6 @@ __device__ __forceinline__ Xf exp_neg(double x) {
     res.m = P << lz;
     res.e = (j ? -1 : 0) + 2 - lz - (int)(n >> 8);
     return res;
-}
-
-// Signed form for polynomial evaluation: value = m * 2^(e - 61) with
-// 2^61 <= |m| < 2^62 (one bit of headroom below the sign), or m == 0 for zero
-// (exponent kXfZeroExp).
-struct XfI {
-    long long m;
-    int e;
-};
-
-// One Horner step t * u + c, for t, c signed and u >= 0 normalised (or zero).
-// The product keeps the high 64 bits of t.m * (u.m / 2) (|p| < 2^61), the sum
-// aligns both terms to the larger exponent (|s| < 2^63) and renormalises.
-// Rounding: 2^-60 relative to the larger term per step.
-__device__ __forceinline__ XfI fma_i(XfI t, Xf u, XfI c) {
-    const long long p = __mul64hi(t.m, (long long)(u.m >> 1));
-    const int ep = t.e + u.e + 2;
-    const int E = max(ep, c.e);
-    const long long s = (p >> min(E - ep, 63)) + (c.m >> min(E - c.e, 63));
-    const unsigned long long a = s < 0 ? 0ULL - (unsigned long long)s : (unsigned long long)s;
-    const int lz = __clzll((long long)a);  // >= 1; 64 for zero
-    XfI r;
-    r.m = lz >= 2 ? (long long)((unsigned long long)s << (lz - 2)) : (s >> 1);
-    r.e = lz >= 2 ? E - (lz - 2) : E + 1;
-    return s == 0 ? XfI{0, kXfZeroExp} : r;
-}
-
-// Finite double -> XfI, exactly (subnormals and zero -> zero).
-__device__ __forceinline__ XfI from_double_signed(double d) {
-    const unsigned long long b = (unsigned long long)__double_as_longlong(d);
-    const int be = (int)((b >> 52) & 0x7FF);
-    const long long m = (long long)(((b & 0xFFFFFFFFFFFFFULL) | 0x10000000000000ULL) << 9);  // [2^61, 2^62)
-    XfI r;
-    r.m = (b >> 63) ? -m : m;
-    r.e = be - 1023;
-    return be == 0 ? XfI{0, kXfZeroExp} : r;
-}
-
-// XfI -> double, rounded to nearest (values in the normal range).
-__device__ __forceinline__ double to_double(XfI v) {
-    const unsigned long long a = v.m < 0 ? 0ULL - (unsigned long long)v.m : (unsigned long long)v.m;
-    const unsigned long long bits = ((unsigned long long)(long long)(v.e + 1022) << 52) + ((a + 256) >> 9);
-    const unsigned long long sgn = v.m < 0 ? 0x8000000000000000ULL : 0ULL;
-    return v.m == 0 ? 0.0 : __longlong_as_double((long long)(bits | sgn));
 }
 
 __device__ __forceinline__ Xf odd(int j) { return Xf{c_odd_m[j], c_odd_e[j]}; }        // 2j+1

@@ -13,7 +13,6 @@ converted by the C library's correctly rounded ``strtod`` semantics (Python
 ``float``), and re-emitted with ``repr`` (shortest round-tripping form), so
 the header holds exactly the doubles the paper specifies.
 """
-import math
 import re
 import struct
 import sys
@@ -102,37 +101,6 @@ def emit(x0, x1, tables, src_name):
         vals = [repr(float(v)) for v in t["den"]] + ["0.0"] * (qmax - len(t["den"]))
         w("  { " + ", ".join(vals) + " }, \\")
     w("}")
-    w("")
-    # the same coefficients in the signed integer-significand format of
-    # boys_xf.cuh: value = m * 2^(e - 61), 2^61 <= |m| < 2^62 (exact: a double's
-    # 53-bit significand fits), zero as (0, -2^28)
-    def xint(v):
-        v = float(v)
-        if v == 0.0:
-            return 0, -(1 << 28)
-        frac, ex = math.frexp(abs(v))
-        m = int(frac * (1 << 62))
-        assert (1 << 61) <= m < (1 << 62) and m * 2.0 ** (ex - 62) == abs(v)
-        return (-m if v < 0 else m), ex - 1
-
-    def rows(vals, n):
-        return [xint(v) for v in vals] + [xint(0.0)] * (n - len(vals))
-
-    w("// P and Q in the signed integer-significand format (value = m * 2^(e-61),")
-    w("// 2^61 <= |m| < 2^62, zero = (0, -2^28)); exact copies of the rows above.")
-    for name, src, n in (("RB_P", rb["num"], pmax), ("RB_Q", rb["den"], qmax)):
-        ms, es = zip(*rows(src, n))
-        w(f"#define BOYS_{name}_XM_INIT {{ " + ", ".join(f"{m}LL" for m in ms) + " }")
-        w(f"#define BOYS_{name}_XE_INIT {{ " + ", ".join(str(e) for e in es) + " }")
-    for name, key, n in (("RA_P", "num", pmax), ("RA_Q", "den", qmax)):
-        w(f"#define BOYS_{name}_XM_INIT {{ \\")
-        for t in ra:
-            w("  { " + ", ".join(f"{m}LL" for m, _ in rows(t[key], n)) + " }, \\")
-        w("}")
-        w(f"#define BOYS_{name}_XE_INIT {{ \\")
-        for t in ra:
-            w("  { " + ", ".join(str(e) for _, e in rows(t[key], n)) + " }, \\")
-        w("}")
     w("")
     return "\n".join(out) + "\n"
 
