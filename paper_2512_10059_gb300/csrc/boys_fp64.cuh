@@ -39,16 +39,17 @@ namespace fp64 {
 
 // Recurrence steps that run in FP64; the rest use the 64-bit-significand
 // integer format (boys_xf.cuh), and e^{-x} always runs on the integer pipes
-// (xf::exp_neg).  The set-up loads the FP64 pipe with the denominator's
-// Horner sum only, the same work at every kmax, while the integer pipes take
-// one step per order, so the balance depends on kmax only (the kernels are
-// branch-free, so not on the argument mix).  Swept on GB300 (stored mode,
-// N = 2^26, kmax 0, 2, 4, 6, 8 and every fourth above x 0..18 FP64 steps):
-// about kmax/2 up to kmax = 16, then (kmax - 4)/2, 14 at kmax = 32 (5.06 ms,
-// against 6.73 with none and 5.19 with 12).  Defining BOYS_FP64_STEPS forces
-// one value for every kmax.
-constexpr int kFp64Steps[33] = {0, 0, 0, 1, 2, 2, 2, 3, 4, 4, 5, 5, 6, 6, 7, 7, 8,
-                                8, 8, 8, 8, 9, 9, 10, 10, 11, 11, 12, 12, 13, 13, 14, 14};
+// (xf::exp_neg).  The set-up's FP64 work (at most the denominator's Horner
+// sum) is the same at every kmax while the integer pipes take one step per
+// order, so the balance depends on kmax only (the kernels are branch-free, so
+// not on the argument mix).  Swept on GB300 (stored mode, N = 2^26, kmax 0,
+// 2, 3, 4, 6, 8 and every fourth above x 0..20 FP64 steps): with the
+// denominator in FP64 (kmax <= 5 and 7) up to 2 steps; with both Horner sums
+// on the integer pipes every step up to kmax = 8, then about (kmax + 4) / 2,
+// 18 at kmax = 32 (4.86 ms, against 6.98 with none and 5.10 with 14).
+// Defining BOYS_FP64_STEPS forces one value for every kmax.
+constexpr int kFp64Steps[33] = {0, 0, 0, 1, 2, 2, 6, 3, 8, 8, 8, 8, 8, 8, 9, 9, 10,
+                                10, 11, 11, 12, 12, 13, 13, 14, 14, 15, 15, 16, 16, 17, 17, 18};
 // The anchor's numerator p runs as a fixed-point Horner sum on the integer
 // pipes for kmax up to BOYS_FIXED_P_MAXK (-1: never), the denominator q in
 // FP64.  A fixed binary point serves the numerators (degree <= 8) to about
@@ -59,6 +60,18 @@ constexpr int kFp64Steps[33] = {0, 0, 0, 1, 2, 2, 2, 3, 4, 4, 5, 5, 6, 6, 7, 7, 
 #ifndef BOYS_FIXED_P_MAXK
 #define BOYS_FIXED_P_MAXK 32
 #endif
+#ifndef BOYS_FIXED_Q_MAXK
+#define BOYS_FIXED_Q_MAXK 32
+#endif
+// Denominators in fixed point from kmax = 6 on, except the degree-13
+// denominator of k = 7: there it adds at most 4.1e-16 to the anchor (the
+// degree-12 and -13 denominators, k = 3, 5, 7, would add up to 2.4e-15), and
+// it pays once the FP64 pipe carries recurrence steps (kmax 8: 2.17 ms against
+// 2.33; kmax 32: 4.86 against 5.06).  Below kmax 6 the FP64 Horner sum costs
+// no time (kmax 0: 1.10 ms against 1.16 in fixed point) and is kept.
+constexpr bool fixed_q_for(int kmax) {
+    return kmax >= 6 && kmax != 7 && kmax <= BOYS_FIXED_Q_MAXK;
+}
 
 constexpr int fp64_steps_for(int kmax) {
 #ifdef BOYS_FP64_STEPS
@@ -88,10 +101,13 @@ static __constant__ double c_ra_q[33][BOYS_RA_QLEN] = BOYS_RA_Q_INIT;
 // r_B padded with zeros to the r_A row lengths
 static __constant__ double c_rb_p[BOYS_RA_PLEN] = BOYS_RB_P_INIT;
 static __constant__ double c_rb_q[BOYS_RA_QLEN] = BOYS_RB_Q_INIT;
-// the numerators in 64-bit fixed point (value = V 2^-f, t = x/16 in A, x/32 in B)
+// the same in 64-bit fixed point (value = V 2^-f, t = x/16 in A, x/32 in B)
 static __constant__ long long c_ra_p_fx[33][BOYS_RA_PLEN] = BOYS_RA_P_FX_INIT;
 static __constant__ long long c_rb_p_fx[BOYS_RA_PLEN] = BOYS_RB_P_FX_INIT;
+static __constant__ long long c_ra_q_fx[33][BOYS_RA_QLEN] = BOYS_RA_Q_FX_INIT;
+static __constant__ long long c_rb_q_fx[BOYS_RA_QLEN] = BOYS_RB_Q_FX_INIT;
 constexpr int kRaPFxf[33] = BOYS_RA_P_FXF_INIT;
+constexpr int kRaQFxf[33] = BOYS_RA_Q_FXF_INIT;
 
 constexpr int cmax(int a, int b) { return a > b ? a : b; }
 
@@ -158,9 +174,10 @@ __device__ __forceinline__ Setup setup_mode(double x) {
     // x/32 (B), t in Q64 (t < 1 on both regions; other lanes get a clamped
     // t whose result is not used), or FP64 Horner.
     constexpr bool kFixedP = KMAX <= BOYS_FIXED_P_MAXK;
-    double p = 0.0;
-    xf::Xf Pfx = xf::zero();
-    if (kFixedP) {
+    constexpr bool kFixedQ = fixed_q_for(KMAX);
+    double p = 0.0, q = 0.0;
+    xf::Xf Pfx = xf::zero(), Qfx = xf::zero();
+    if (kFixedP || kFixedQ) {
         const unsigned long long xbu = (unsigned long long)xb;
         const int be = (int)((xbu >> 52) & 0x7FF);
         const unsigned long long mant = (xbu & 0xFFFFFFFFFFFFFULL) | 0x10000000000000ULL;
@@ -168,19 +185,31 @@ __device__ __forceinline__ Setup setup_mode(double x) {
         unsigned long long T = sh >= 0 ? (mant << min(sh, 11)) : (mant >> min(-sh, 63));
         if (be == 0) T = 0;
         const unsigned long long Th = T >> 1;
-        long long v = inA ? c_ra_p_fx[KMAX][NP] : c_rb_p_fx[NP];
+        if (kFixedP) {
+            long long v = inA ? c_ra_p_fx[KMAX][NP] : c_rb_p_fx[NP];
 #pragma unroll
-        for (int i = NP - 1; i >= 0; --i) v = xf::mulhi_s(v, T, Th) + (inA ? c_ra_p_fx[KMAX][i] : c_rb_p_fx[i]);
-        constexpr int kFa = kRaPFxf[KMAX];
-        Pfx = xf::from_fixed(v, inA ? kFa : BOYS_RB_P_FXF);
-    } else {
+            for (int i = NP - 1; i >= 0; --i) v = xf::mulhi_s(v, T, Th) + (inA ? c_ra_p_fx[KMAX][i] : c_rb_p_fx[i]);
+            constexpr int kFa = kRaPFxf[KMAX];
+            Pfx = xf::from_fixed(v, inA ? kFa : BOYS_RB_P_FXF);
+        }
+        if (kFixedQ) {
+            long long v = inA ? c_ra_q_fx[KMAX][NQ] : c_rb_q_fx[NQ];
+#pragma unroll
+            for (int i = NQ - 1; i >= 0; --i) v = xf::mulhi_s(v, T, Th) + (inA ? c_ra_q_fx[KMAX][i] : c_rb_q_fx[i]);
+            constexpr int kFa = kRaQFxf[KMAX];
+            Qfx = xf::from_fixed(v, inA ? kFa : BOYS_RB_Q_FXF);
+        }
+    }
+    if (!kFixedP) {
         p = inA ? c_ra_p[KMAX][NP] : c_rb_p[NP];
 #pragma unroll
         for (int i = NP - 1; i >= 0; --i) p = fma(p, x, inA ? c_ra_p[KMAX][i] : c_rb_p[i]);
     }
-    double q = inA ? c_ra_q[KMAX][NQ] : c_rb_q[NQ];
+    if (!kFixedQ) {
+        q = inA ? c_ra_q[KMAX][NQ] : c_rb_q[NQ];
 #pragma unroll
-    for (int i = NQ - 1; i >= 0; --i) q = fma(q, x, inA ? c_ra_q[KMAX][i] : c_rb_q[i]);
+        for (int i = NQ - 1; i >= 0; --i) q = fma(q, x, inA ? c_ra_q[KMAX][i] : c_rb_q[i]);
+    }
 
     // Arguments beyond 1e300 are clamped there in C (F_0 < 1e-150 and F_k = 0
     // for k > 0 either way); +inf gives exactly 0.
@@ -191,7 +220,7 @@ __device__ __forceinline__ Setup setup_mode(double x) {
     // format (integer pipes): r = z^{-1/2} with z = q^2 (A), (2x q)^2 (B), x (C).
     // p/q > 0 on both regions, so magnitudes suffice (from_double drops signs).
     const xf::Xf P = kFixedP ? Pfx : xf::from_double(p);
-    const xf::Xf Q = xf::from_double(q);
+    const xf::Xf Q = kFixedQ ? Qfx : xf::from_double(q);
     xf::Xf y0, R;
     if (MODE == kRegionNone) {
         const xf::Xf tq = inA ? Q : xf::mul(X2, Q);

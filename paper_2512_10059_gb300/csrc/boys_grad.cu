@@ -18,10 +18,10 @@ constexpr int kBlock = 128;
 
 // FP64 recurrence steps and minimum resident blocks of the gradient kernel
 // (its own g_k F_{k+1} sum is FP64 work already): swept on GB300 at kmax 16,
-// N = 2^24: no FP64 step and 8 blocks per SM (64 registers), 1.11 ms, against
-// 1.23 with the register count left free and 1.21 with 2 FP64 steps.
+// N = 2^24: 4 FP64 steps and 8 blocks per SM (64 registers), 1.04 ms, against
+// 1.12 with none, 1.10 with 8 and 1.23 with the register count left free.
 #ifndef BOYS_GRAD_FP64_STEPS
-#define BOYS_GRAD_FP64_STEPS 0
+#define BOYS_GRAD_FP64_STEPS 4
 #endif
 #ifndef BOYS_GRAD_MIN_BLOCKS
 #define BOYS_GRAD_MIN_BLOCKS 8

@@ -1,15 +1,20 @@
-"""The fixed-point numerator Horner of the set-up (csrc/boys_fp64.cuh with
+"""The fixed-point Horner sums of the set-up (csrc/boys_fp64.cuh with
 csrc/boys_coeffs_fixed.h), modelled with Python integers exactly as the
-device runs it: t = x/16 (region A) or x/32 (region B) in Q64, the
+device runs them: t = x/16 (region A) or x/32 (region B) in Q64, the
 three-partial-product high product of xf::mulhi3, the signed product by the
 biased operand (v + 2^63) t / 2^64 - t/2, and the per-polynomial binary point.
 
-Checked against exact rational evaluation of the Appendix D rationals: the
-anchor p_fixed / q - p / q must stay within 2e-16 for r_{A,0} (whose value is
-near 1), 3e-17 for every other r_{A,k} and 5e-17 for r_B, a few hundredths of
-the 5e-14 budget at most, and every Horner intermediate below 2^62.  Two
-planted mistakes (the bias correction dropped, the binary point off by one)
-must fail the same bound.
+Checked against exact rational evaluation of the Appendix D rationals, one
+sum fixed and the other exact:
+* numerators: p_fixed / q - p / q within 2e-16 for r_{A,0} (whose value is
+  near 1), 3e-17 for every other r_{A,k} and 5e-17 for r_B;
+* denominators, at every order but the degree-12 and -13 denominators
+  (k = 3, 5, 7; the kernels use fixed-point denominators from kmax 6 on,
+  except 7): p / q_fixed - p / q within 5e-16 for every r_{A,k} and 5e-17
+  for r_B;
+at most 1% of the 5e-14 budget, with every Horner intermediate below 2^62.
+Planted mistakes (the bias correction dropped, the binary point off by one)
+must fail the same bounds.
 """
 import importlib.util
 import os
@@ -31,13 +36,14 @@ def _gen():
     return mod
 
 
-def _tables():
+def _tables(name="P"):
     s = open(os.path.join(CSRC, "boys_coeffs_fixed.h")).read()
-    body = re.search(r"#define BOYS_RA_P_FX_INIT \{ \\\n(.*?)\n\}", s, re.S).group(1)
+    body = re.search(r"#define BOYS_RA_" + name + r"_FX_INIT \{ \\\n(.*?)\n\}", s, re.S).group(1)
     ra = [[int(v.strip().rstrip("L")) for v in r.split(",")] for r in re.findall(r"\{ (.*?) \}", body)]
-    rb = [int(v.strip().rstrip("L")) for v in re.search(r"#define BOYS_RB_P_FX_INIT \{ (.*?) \}", s).group(1).split(",")]
-    fa = [int(v) for v in re.search(r"#define BOYS_RA_P_FXF_INIT \{ (.*?) \}", s).group(1).split(",")]
-    fb = int(re.search(r"#define BOYS_RB_P_FXF (-?\d+)", s).group(1))
+    rb = [int(v.strip().rstrip("L")) for v in
+          re.search(r"#define BOYS_RB_" + name + r"_FX_INIT \{ (.*?) \}", s).group(1).split(",")]
+    fa = [int(v) for v in re.search(r"#define BOYS_RA_" + name + r"_FXF_INIT \{ (.*?) \}", s).group(1).split(",")]
+    fb = int(re.search(r"#define BOYS_RB_" + name + r"_FXF (-?\d+)", s).group(1))
     return ra, fa, rb, fb
 
 
@@ -55,7 +61,7 @@ def _horner(A, deg, t, bias=True, check_range=True):
     return v
 
 
-def _worst(A, deg, f, pc, qc, lo, hi, shift, **kw):
+def _worst(A, deg, f, pc, qc, lo, hi, shift, fixed_q=False, **kw):
     xs = list(np.linspace(lo, hi, 240, endpoint=False)) + [hi * (1 - 2.0 ** -50), 1e-300, 1e-9]
     w = 0.0
     for x in xs:
@@ -63,10 +69,10 @@ def _worst(A, deg, f, pc, qc, lo, hi, shift, **kw):
             continue
         X = Fraction(x)
         t = int(X * 2 ** (64 - shift))      # the device's shifted significand, exact for x < 2^shift
-        P = Fraction(_horner(A, deg, t, **kw), 2 ** f)
+        V = Fraction(_horner(A, deg, t, **kw), 2 ** f)
         Pe = sum(Fraction(c) * X ** i for i, c in enumerate(pc))
         Qe = sum(Fraction(c) * X ** i for i, c in enumerate(qc))
-        w = max(w, abs(float((P - Pe) / Qe)))
+        w = max(w, abs(float(Pe / V - Pe / Qe)) if fixed_q else abs(float((V - Pe) / Qe)))
     return w
 
 
@@ -83,6 +89,25 @@ def test_fixed_numerators_error_bound():
     assert _worst(rb, 5, fb, T["rb_p"], T["rb_q"], T["x0"], T["x1"], 5) <= 5e-17
 
 
+def test_fixed_denominators_error_bound():
+    T = boys_header.load()
+    ra, fa, rb, fb = _tables("Q")
+    for k in range(33):
+        if k in (3, 5, 7):
+            continue
+        w = _worst(ra[k], T["ra_m"][k], fa[k], T["ra_p"][k], T["ra_q"][k], 0.0, T["x0"], 4, fixed_q=True)
+        assert w <= 5e-16, (k, w)
+    assert _worst(rb, 6, fb, T["rb_p"], T["rb_q"], T["x0"], T["x1"], 5, fixed_q=True) <= 5e-17
+
+
+def test_fixed_denominators_excluded_orders_are_the_ones_that_need_it():
+    """The three orders kept in FP64 would add more than the bound above."""
+    T = boys_header.load()
+    ra, fa, _, _ = _tables("Q")
+    for k in (3, 5, 7):
+        assert _worst(ra[k], T["ra_m"][k], fa[k], T["ra_p"][k], T["ra_q"][k], 0.0, T["x0"], 4, fixed_q=True) > 5e-16
+
+
 def test_planted_mistakes_fail():
     T = boys_header.load()
     ra, fa, _, _ = _tables()
@@ -90,3 +115,5 @@ def test_planted_mistakes_fail():
     args = (T["ra_p"][k], T["ra_q"][k], 0.0, T["x0"], 4)
     assert _worst(ra[k], T["ra_n"][k], fa[k], *args, bias=False, check_range=False) > 1e-12
     assert _worst(ra[k], T["ra_n"][k], fa[k] - 1, *args, check_range=False) > 1e-12
+    rq, fq, _, _ = _tables("Q")
+    assert _worst(rq[k], T["ra_m"][k], fq[k] + 1, *args, fixed_q=True, check_range=False) > 1e-12
