@@ -60,9 +60,9 @@ HBM_FALLBACK_GBS = 6800.0
 # (profiles/k_eval_f64_kmax32_eri_mixture.md), scaled to the launch by the
 # arguments it processes.  Valid only for the kernel sources it was taken on:
 # the bench reports traffic null whenever their SHA-256 differs.
-TRAFFIC_CAPTURE = {"bytes_per_x": 257.57, "sources_sha256": "29200f1a26ee7b89683e883df1e78fb857087ecdefb9dae1cbca54ea53e380d1"}
+TRAFFIC_CAPTURE = {"bytes_per_x": 257.57, "sources_sha256": "0ddb3e68a4cd4ddd5a7adde9148a0fb7566bd9e08a7139748da51fe6ea5ac266"}
 KERNEL_SOURCES = ("boys_fp64.cu", "boys_fp64.cuh", "boys_xf.cuh", "boys_math.cuh", "boys_coeffs_fp64.h",
-                  "boys_xf_consts.h", "boys_exp_table.h")
+                  "boys_coeffs_fixed.h", "boys_xf_consts.h", "boys_exp_table.h")
 
 
 def kernel_sources_sha256():
@@ -503,7 +503,12 @@ def run_ours(args):
         o3 = torch.empty_like(plan.out)
         pl_ms = time_launches(lambda: pb.boys_eval_ragged(xt3, ot3, kt3, out=o3, out_off=plan.out_off, workspace=ws3),
                               max(5, min(args.steps, 20)))
-        del ws3, o3
+        # and with a 256-byte workspace: the persistent kernel (the shape
+        # boys_eval_ragged_noalloc uses)
+        ws_small = torch.empty(256, dtype=torch.uint8, device=dev)
+        ps_ms = time_launches(lambda: pb.boys_eval_ragged(xt3, ot3, kt3, out=o3, out_off=plan.out_off,
+                                                          workspace=ws_small), max(5, min(args.steps, 20)))
+        del ws3, o3, ws_small
         lens = np.diff(off3)
         nval = int(np.sum((km3.astype(np.int64) + 1) * lens))
         rbytes = 8 * x3.size + 8 * nval + 20 * km3.size
@@ -512,7 +517,7 @@ def run_ours(args):
                   "segments": int(km3.size), "mean_kmax_weighted": float(np.sum(km3 * lens) / lens.sum()),
                   "hbm_gbs": rbytes / (rms / 1e3) / 1e9,
                   "fp64_frac": rfl / (rms / 1e3) / 1e12 / FP64_PEAK_TFLOPS, "config": plan.config(),
-                  "planless_ms": pl_ms, "planless_vs_plan": pl_ms / rms,
+                  "planless_ms": pl_ms, "planless_vs_plan": pl_ms / rms, "persistent_ms": ps_ms,
                   "launch": "one cudaGraphLaunch: workspace memset + " +
                             ("one kernel per kmax group (parallel graph branches)" if plan.config()["waves"] == 0
                              else "persistent kernel")}

@@ -112,8 +112,11 @@ boys_status boys_eval_fused(const double* x, const double* rho, int64_t n, int k
  * set per kmax: x0(kmax) from Eq. x0, x1(kmax) from Eq. x1 with a 3e-7
  * asymptotic budget.  Absolute accuracy 1e-6 for every order against the
  * exact F_k at the (float) input.  x float [n]; out float [kmax+1][ld];
- * 0 <= kmax <= 32; 16-byte alignment of x and out and ld % 4 == 0 enable
- * 128-bit accesses.
+ * 0 <= kmax <= 32.  Alignment and kmax choose the access width, never the
+ * results: below kmax 8, 16-byte aligned x and out with ld % 4 == 0 give
+ * 128-bit accesses (four arguments per thread); otherwise 8-byte aligned x
+ * and out with even ld give 64-bit accesses (two per thread); anything else
+ * 32-bit accesses.
  */
 boys_status boys_eval_f32(const float* x, int64_t n, int kmax, float* out, int64_t ld, void* stream);
 

@@ -59,16 +59,25 @@ def test_every_kmax(T, kmax):
     _check(xf, _eval(xf, kmax), kmax)
 
 
+@pytest.mark.parametrize("kmax", [5, 9])
 @pytest.mark.parametrize("n", [1, 3, 4, 5, 127, 129, 511, 513, 4099])
-def test_sizes_tails_and_vector_path(n):
+def test_sizes_tails_and_vector_path(n, kmax):
+    """kmax 5 runs four arguments per thread (16-byte vectors), kmax 9 two
+    (8-byte vectors); both must agree bitwise with the 8-byte and scalar paths."""
     xf = W.mixture_c2(n, seed=13).astype(np.float32)
-    got = _eval(xf, 9)
-    _check(xf, got, 9)
-    base = torch.from_numpy(np.concatenate([[0.0], xf]).astype(np.float32)).to(DEV)
-    out = torch.empty((10, n + 1), dtype=torch.float32, device=DEV)[:, :n]
-    pb.boys_eval_f32(base[1:], 9, out=out)   # 4-byte aligned only, odd ld: scalar path
+    got = _eval(xf, kmax)
+    _check(xf, got, kmax)
+    base1 = torch.from_numpy(np.concatenate([[0.0], xf]).astype(np.float32)).to(DEV)
+    out = torch.empty((kmax + 1, n + 1), dtype=torch.float32, device=DEV)[:, :n]
+    pb.boys_eval_f32(base1[1:], kmax, out=out)    # x 4-byte aligned only: scalar path
     torch.cuda.synchronize()
     assert np.array_equal(out.cpu().numpy(), got)
+    base2 = torch.from_numpy(np.concatenate([[0.0, 0.0], xf]).astype(np.float32)).to(DEV)
+    ld = n + 4 + (n % 2)                           # even ld, 8-byte aligned starts: 2-vector path
+    out2 = torch.empty((kmax + 1, ld), dtype=torch.float32, device=DEV)[:, 2:2 + n]
+    pb.boys_eval_f32(base2[2:], kmax, out=out2)
+    torch.cuda.synchronize()
+    assert np.array_equal(out2.cpu().numpy(), got)
 
 
 def test_special_values():
