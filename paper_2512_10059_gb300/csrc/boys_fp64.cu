@@ -14,24 +14,27 @@
 #include "boys_internal.h"
 
 // Minimum resident blocks per SM of the stored-mode kernel, which caps its
-// registers: swept on GB300 with the FP64-step table of boys_fp64.cuh, 12
-// blocks (40 registers) up to kmax = 7, 10 (48) up to 16 and 8 (64) above
-// (kmax 8: 2.33 ms with 10 against 2.38 with 8 and 2.34 with 12; kmax 16:
-// 3.26 with 10 against 3.30 with 8; kmax 32: 5.30 with 8 against 5.45 with 9).
+// registers: swept on GB300 with the FP64-step table of boys_fp64.cuh
+// (N = 2^26, 8, 9, 10, 12 and 14 blocks at kmax 2, 4, 6, 8, 12, 16, 20, 24,
+// 28): up to kmax = 20 the 32-register cap of full occupancy is fastest
+// despite its spills to L1 (kmax 4: 1.86 ms against 1.91 with 8 and 1.90
+// with 12; kmax 12: 2.54 against 2.59 and 2.58; kmax 20: 3.33 against 3.39),
+// from kmax 24 on 8 blocks (64 registers) win (kmax 24: 3.79 against 4.22
+// with 14; kmax 32: 4.68 against 4.68 with 9 and 4.78 with 7).
 // BOYS_STORED_MIN_BLOCKS forces one value.
 constexpr int stored_min_blocks(int kmax) {
 #ifdef BOYS_STORED_MIN_BLOCKS
     return BOYS_STORED_MIN_BLOCKS + 0 * kmax;
 #else
-    return kmax <= 7 ? 12 : (kmax <= 16 ? 10 : 8);
+    return kmax <= 20 ? 16 : 8;
 #endif
 }
 // FP64 recurrence steps and minimum resident blocks of the fused kernel.  Its
 // Horner sum adds KMAX FMAs per argument to the FP64 pipe, so half of stored
-// mode's FP64 steps run in FP64 (swept on GB300 at kmax 32, N = 2^26: 0 steps
-// 7.84 ms, 4 7.41, 6 7.36, 8 7.34; 6 blocks per SM 7.53, 10 8.07; the
-// smaller kmax follow the stored-mode table).  BOYS_FUSED_FP64_STEPS forces
-// one value.
+// mode's FP64 steps run in FP64 (swept on GB300 at kmax 32, N = 2^26: 5 steps
+// 6.82 ms, 7 6.68, 8 6.67, 9 6.69, 11 6.84, 13 7.19; 6 and 10 blocks per SM
+// were slower than 8; the smaller kmax follow the stored-mode table).
+// BOYS_FUSED_FP64_STEPS forces one value.
 constexpr int fused_fp64_steps(int kmax) {
 #ifdef BOYS_FUSED_FP64_STEPS
     return BOYS_FUSED_FP64_STEPS + 0 * kmax;

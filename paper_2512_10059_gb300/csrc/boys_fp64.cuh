@@ -42,14 +42,14 @@ namespace fp64 {
 // (xf::exp_neg).  The set-up's FP64 work (at most the denominator's Horner
 // sum) is the same at every kmax while the integer pipes take one step per
 // order, so the balance depends on kmax only (the kernels are branch-free, so
-// not on the argument mix).  Swept on GB300 (stored mode, N = 2^26, kmax 0,
-// 2, 3, 4, 6, 8 and every fourth above x 0..20 FP64 steps): with the
-// denominator in FP64 (kmax <= 5 and 7) up to 2 steps; with both Horner sums
-// on the integer pipes every step up to kmax = 8, then about (kmax + 4) / 2,
-// 18 at kmax = 32 (4.86 ms, against 6.98 with none and 5.10 with 14).
+// not on the argument mix).  Swept on GB300 (stored mode, N = 2^26, every kmax
+// x 0..22 FP64 steps, median of 3): with the denominator in FP64 (kmax <= 5
+// and 7) at most 2 steps; with both Horner sums on the integer pipes every
+// step up to kmax = 8, then about kmax / 2 + 1, 17 at kmax = 32 (4.69 ms,
+// against 6.33 with none and 4.81 with 14 or 5.16 with 20).
 // Defining BOYS_FP64_STEPS forces one value for every kmax.
-constexpr int kFp64Steps[33] = {0, 0, 0, 1, 2, 2, 6, 3, 8, 8, 8, 8, 8, 8, 9, 9, 10,
-                                10, 11, 11, 12, 12, 13, 13, 14, 14, 15, 15, 16, 16, 17, 17, 18};
+constexpr int kFp64Steps[33] = {0, 0, 0, 0, 2, 0, 6, 2, 8, 8, 8, 8, 9, 9, 10, 10, 10,
+                                11, 11, 11, 12, 12, 13, 13, 13, 13, 14, 14, 15, 15, 16, 16, 17};
 // The anchor's numerator p runs as a fixed-point Horner sum on the integer
 // pipes for kmax up to BOYS_FIXED_P_MAXK (-1: never), the denominator q in
 // FP64.  A fixed binary point serves the numerators (degree <= 8) to about
@@ -240,7 +240,10 @@ __device__ __forceinline__ Setup setup_mode(double x) {
         y0 = xf::mul(xf::sqrt_pi_over_2(), r);
         R = xf::mul(xf::Xf{r.m, r.e - 1}, r);
     }
-    if (xb == kBitsInf) y0 = xf::zero();
+    // +inf gives exactly 0; an invalid argument starts the integer-format
+    // recurrence from zero (its values flush to NaN in out_value) and the
+    // FP64 one from NaN, which every FP64 step propagates.
+    if (xb == kBitsInf || !valid) y0 = xf::zero();
     // e^{-x}: on the integer pipes, straight into the recurrence's format, when
     // no step runs in FP64 (the FP64 copy is then only assembled if used)
     double e;
@@ -257,7 +260,7 @@ __device__ __forceinline__ Setup setup_mode(double x) {
     S.valid = valid;
     S.inA = inA;
     S.y0 = y0;
-    S.y0d = xf::to_double(y0);
+    S.y0d = valid ? xf::to_double(y0) : quiet_nan();
     S.X2 = X2;
     S.two_x = xf::to_double(X2);
     S.sd = inC ? 0.0 : (inA ? e : -e);
@@ -290,7 +293,7 @@ __device__ __forceinline__ xf::Xf step(const Setup& S, int j, xf::Xf y) {
     const int l = KMAX - 1 - j;
     const xf::Xf a = xf::select(S.inA, S.X2, xf::odd(j));
     const xf::Xf c = xf::select(S.inA, xf::recip_odd(l), S.R);
-    return xf::mul(xf::add_prepared(xf::mul_raw(a, y), S.Es), c);
+    return xf::mul_norm(xf::add_raw(xf::mul_raw(a, y), S.Es), c);
 }
 
 // One select per output: NaN for an invalid argument, 0 below the normal
@@ -310,15 +313,17 @@ __device__ __forceinline__ double step_fp64(const Setup& S, int j, double y) {
 }
 
 // Value number p of the recurrence (p = 0: the anchor; FP64 for p <= NF64,
-// the integer format after), advancing yd / y in place.
+// the integer format after), advancing yd / y in place.  FP64 values need no
+// select: an invalid argument's yd is NaN from the anchor on.
 template <int KMAX, int NSTEPS_FP64 = fp64_steps_for(KMAX)>
 __device__ __forceinline__ double next_value(const Setup& S, int p, double& yd, xf::Xf& y) {
     constexpr int NF64 = NSTEPS_FP64 < KMAX ? NSTEPS_FP64 : KMAX;
     if (p <= NF64) {
         if (p > 0) yd = step_fp64<KMAX>(S, p - 1, yd);
-        return S.valid ? yd : quiet_nan();
+        return yd;
     }
-    y = step<KMAX>(S, p - 1, p - 1 == NF64 ? xf::from_double(yd) : y);
+    if (p - 1 == NF64 && p > 1) y = S.valid ? xf::from_double(yd) : xf::zero();
+    y = step<KMAX>(S, p - 1, y);
     return out_value(S, y);
 }
 
@@ -358,6 +363,11 @@ __device__ __forceinline__ void eval_store(double x, double* __restrict__ col, i
     constexpr int H = KMAX / 2 + 1;
     const Setup S = setup<KMAX, int_exp_for(KMAX, fp64_steps_for(KMAX))>(x);
     double hold[H];
+    // Value p belongs to row KMAX - p on an A lane and to row p otherwise:
+    // row colp + p sld on every lane, and the held value's row colp + q sld
+    // (q = KMAX - p), with a lane's base and row stride chosen once.
+    double* const colp = S.inA ? col + (int64_t)KMAX * ld : col;
+    const int64_t sld = S.inA ? -ld : ld;
     double yd = S.y0d;
     xf::Xf y = S.y0;
 #pragma unroll
@@ -366,21 +376,21 @@ __device__ __forceinline__ void eval_store(double x, double* __restrict__ col, i
         if (2 * p < KMAX) {
             hold[p] = v;
         } else if (2 * p == KMAX) {
-            __stcs(col + p * ld, v);
+            __stcs(colp + p * sld, v);
         } else {
             // rows p and q = KMAX - p: this step's value is F_q on an A lane and
-            // F_p otherwise; the held one is the other.  Selecting the row (an
-            // IMAD on the FMA pipe) instead of the value (two SELs per double on
-            // the ALU) makes each store write two half rows, which L2 merges
-            // before DRAM (kmax 32: 5.32 -> 5.24 ms).
+            // F_p otherwise; the held one is the other.  Picking the row per
+            // lane (an address IMAD on the FMA pipe) instead of the value (two
+            // SELs per double on the ALU) makes each store write two half rows,
+            // which L2 merges before DRAM (kmax 32: 5.32 -> 5.24 ms; the lane's
+            // base and stride instead of a row select per store: 4.68 -> 4.65).
             const int q = KMAX - p;
             if (FULL_ROWS) {
                 __stcs(col + p * ld, S.inA ? hold[q] : v);
                 __stcs(col + q * ld, S.inA ? v : hold[q]);
             } else {
-                const int64_t rv = S.inA ? q : p;
-                __stcs(col + rv * ld, v);
-                __stcs(col + (KMAX - rv) * ld, hold[q]);
+                __stcs(colp + p * sld, v);
+                __stcs(colp + q * sld, hold[q]);
             }
         }
     }

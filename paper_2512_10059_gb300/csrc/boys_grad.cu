@@ -18,8 +18,9 @@ constexpr int kBlock = 128;
 
 // FP64 recurrence steps and minimum resident blocks of the gradient kernel
 // (its own g_k F_{k+1} sum is FP64 work already): swept on GB300 at kmax 16,
-// N = 2^24: 4 FP64 steps and 8 blocks per SM (64 registers), 1.04 ms, against
-// 1.12 with none, 1.10 with 8 and 1.23 with the register count left free.
+// N = 2^24: 4 FP64 steps and 8 blocks per SM (64 registers), 1.00 ms, against
+// 1.03 with 2, 1.02 with 6, 1.09 with 8 and, with an earlier step, 1.23 with
+// the register count left free.
 #ifndef BOYS_GRAD_FP64_STEPS
 #define BOYS_GRAD_FP64_STEPS 4
 #endif

@@ -191,7 +191,14 @@ struct Tile {
 };
 static_assert(sizeof(Tile) == 16, "tile table entries are 16 bytes");
 
-constexpr int grouped_min_blocks(int kmax) { return kmax <= 16 ? 5 : 4; }  // 48 / 64 registers at 256 threads
+// 48 / 64 registers at 256 threads; BOYS_GROUPED_MIN_BLOCKS forces one value
+constexpr int grouped_min_blocks(int kmax) {
+#ifdef BOYS_GROUPED_MIN_BLOCKS
+    return BOYS_GROUPED_MIN_BLOCKS + 0 * kmax;
+#else
+    return kmax <= 16 ? 5 : 4;
+#endif
+}
 
 // One tile of a kmax group: its arguments, one per thread.
 template <int K>

@@ -16,13 +16,14 @@
 //    three 32 x 32-bit partial products (mulhi3: at most 2 units of 2^-64
 //    below the exact high half);
 //  * a sum aligns both terms to the larger exponent, one bit below the top,
-//    and renormalises with a 32-bit leading-zero count of the high word: the
-//    recurrences never cancel more than two leading bits (the upward step
-//    (2j+1) F_j - e^{-x} keeps at least 0.36 of (2j+1) F_j on region B, and
-//    the downward step adds two positive terms), so the leading bit of a sum
-//    always lies in the high word;
-//  * the product feeding an addition skips its own renormalisation, and the
-//    addend e^{-x} is shifted and signed once per argument.
+//    and is left unnormalised: the recurrences never cancel more than two
+//    leading bits (the upward step (2j+1) F_j - e^{-x} keeps at least 0.36
+//    of (2j+1) F_j on region B, and the downward step adds two positive
+//    terms), so a sum keeps its leading bit within its top four bits;
+//  * the product that follows a sum renormalises by a 32-bit leading-zero
+//    count of its high word, so a recurrence step renormalises once; the
+//    product feeding a sum skips renormalisation, and the addend e^{-x} is
+//    shifted and signed once per argument.
 #pragma once
 
 #include <cstdint>
@@ -124,22 +125,44 @@ __device__ __forceinline__ XfS prepare_addend(Xf s, bool negate) {
     return XfS{negate ? -v : v, s.e};
 }
 
+// Logical and arithmetic right shifts by n >= 0 with PTX semantics: shift
+// counts of 64 and more give 0 (or the sign), so no clamp is needed.
+__device__ __forceinline__ unsigned long long shr_u64(unsigned long long a, int n) {
+    unsigned long long r;
+    asm("shr.b64 %0, %1, %2;" : "=l"(r) : "l"(a), "r"(n));
+    return r;
+}
+__device__ __forceinline__ long long shr_s64(long long a, int n) {
+    long long r;
+    asm("shr.s64 %0, %1, %2;" : "=l"(r) : "l"(a), "r"(n));
+    return r;
+}
+
 // t + s for a raw product t (m in [2^62, 2^64), or zero) and a prepared
 // signed addend s, where either both terms are >= 0 or the exact sum is at
-// least a quarter of t (the recurrences' cases: the sum's leading bit then
-// lies in bits 59..63).  Both terms are aligned to 2^(E - 62), E the larger
-// exponent (t one bit below the top, so two positive terms cannot carry out),
-// added modulo 2^64 and renormalised by a leading-zero count of the high word.
-// A zero sum stays zero (m = 0, exponent near kXfZeroExp).
-__device__ __forceinline__ Xf add_prepared(Xf t, XfS s) {
+// least a quarter of t (the recurrences' cases).  Both terms are aligned to
+// 2^(E - 62), E the larger exponent (t one bit below the top, so two positive
+// terms cannot carry out), and added modulo 2^64.  The result is left
+// unnormalised for mul_norm: m = u with its leading bit in bits 59..63
+// (u >= t/4 >= 2^59 after the alignment), e = E + 1.  A zero sum stays zero
+// (m = 0, exponent near kXfZeroExp).
+__device__ __forceinline__ Xf add_raw(Xf t, XfS s) {
     const int E = max(t.e, s.e);
-    const unsigned long long ta = t.m >> min(E - t.e + 1, 63);
-    const long long sa = s.m >> min(E - s.e, 63);  // arithmetic shift keeps the sign
-    const unsigned long long u = ta + (unsigned long long)sa;
-    const int lz = __clz((int)(u >> 32));          // 0..4 for the recurrences; 32 for zero
+    const unsigned long long ta = shr_u64(t.m, E - t.e + 1);
+    const long long sa = shr_s64(s.m, E - s.e);  // arithmetic shift keeps the sign
+    return Xf{ta + (unsigned long long)sa, E + 1};
+}
+
+// a b for an operand a with at most four leading zeros (a sum from add_raw)
+// and a normalised b, renormalised by a 32-bit leading-zero count of the high
+// word (the product's leading bit lies in bits 57..63; zero stays zero).
+// With the leading zeros of a the product keeps about 59 significant bits.
+__device__ __forceinline__ Xf mul_norm(Xf a, Xf b) {
+    const unsigned long long hi = mulhi3(a.m, b.m);
+    const int lz = __clz((int)(hi >> 32));
     Xf r;
-    r.m = u << lz;
-    r.e = E + 1 - lz;
+    r.m = hi << lz;
+    r.e = a.e + b.e + 1 - lz;
     return r;
 }
 
