@@ -88,6 +88,23 @@ def test_special_values():
     _check(x[4:], got[:, 4:], 32, "special")
 
 
+@pytest.mark.parametrize("kmax", list(range(33)))
+def test_invalid_and_infinite_every_kmax(kmax):
+    """Every FP64/integer split: an invalid argument (NaN, negative, -inf)
+    gives NaN in every order, from the FP64 steps and from the integer-format
+    ones alike; +inf gives 0; valid neighbours in the same warp are unaffected."""
+    x = np.array([np.nan, -1.0, -1e-300, -np.inf, np.inf, 0.0, 1.0, 20.0, 40.0, 5.0] * 4)
+    got = _eval(x, kmax)
+    bad = np.isnan(x) | (x < 0)
+    assert np.all(np.isnan(got[:, bad]))
+    assert np.all(got[:, np.isposinf(x)] == 0.0)
+    ok = ~bad & np.isfinite(x)
+    _check(x[ok], got[:, ok], kmax, "invalid neighbours")
+    rho = np.full(x.size, 0.75)
+    fz = pb.boys_eval_fused(torch.from_numpy(x).to(DEV), torch.from_numpy(rho).to(DEV), kmax).cpu().numpy()
+    assert np.all(np.isnan(fz[bad])) and np.all(np.isfinite(fz[~bad]))
+
+
 def test_bitwise_deterministic():
     x = W.mixture_c2(100000, seed=3)
     a = _eval(x, 32)
