@@ -96,10 +96,13 @@ boys_status boys_eval(const double* x, int64_t n, int kmax, double* out, int64_t
 boys_status boys_eval_host(const double* x, int64_t n, int kmax, double* out, int64_t ld, void* stream);
 
 /*
- * FP64 fused consumer — the F_k never leave registers:
+ * FP64 fused consumer — the F_k never leave the SM (registers and 16 KB of
+ * shared memory per 128-thread block at kmax 32):
  *   out[i] = sum_{k=0}^{kmax} (-2 rho_i)^k F_k(x_i)
  * (the McMurchie-Davidson-style scaling of an electron-repulsion-integral
- * kernel; the F_k are evaluated exactly as boys_eval does).
+ * kernel; the F_k are evaluated as boys_eval does, to the same accuracy).
+ * The sum is formed as two Horner sums in a = -2 rho joined by a^(kmax/2+1),
+ * so |2 rho|^(kmax/2+1) must be finite in double precision.
  *   x, rho [n] inputs; out [n] output; 0 <= kmax <= 32.
  */
 boys_status boys_eval_fused(const double* x, const double* rho, int64_t n, int kmax,

@@ -30,11 +30,12 @@ constexpr int stored_min_blocks(int kmax) {
 #endif
 }
 // FP64 recurrence steps and minimum resident blocks of the fused kernel.  Its
-// Horner sum adds KMAX FMAs per argument to the FP64 pipe, so half of stored
-// mode's FP64 steps run in FP64 (swept on GB300 at kmax 32, N = 2^26: 5 steps
-// 6.82 ms, 7 6.68, 8 6.67, 9 6.69, 11 6.84, 13 7.19; 6 and 10 blocks per SM
-// were slower than 8; the smaller kmax follow the stored-mode table).
-// BOYS_FUSED_FP64_STEPS forces one value.
+// Horner sums add KMAX + 1 FMAs per argument to the FP64 pipe, so half of
+// stored mode's FP64 steps run in FP64.  Swept on GB300 at kmax 32, N = 2^26
+// (ms per launch): 8 blocks per SM with 6, 8, 10, 12 steps 6.65, 6.65, 6.79,
+// 7.19; 8 steps with 4, 5, 6, 7, 10, 12 blocks 6.50, 6.58, 6.50, 6.65, 6.78,
+// 6.75; 6 blocks with 6, 7, 9, 10 steps 6.56, 6.50, 6.57, 6.75.  The smaller
+// kmax follow the stored-mode table.  BOYS_FUSED_FP64_STEPS forces one value.
 constexpr int fused_fp64_steps(int kmax) {
 #ifdef BOYS_FUSED_FP64_STEPS
     return BOYS_FUSED_FP64_STEPS + 0 * kmax;
@@ -43,7 +44,7 @@ constexpr int fused_fp64_steps(int kmax) {
 #endif
 }
 #ifndef BOYS_FUSED_MIN_BLOCKS
-#define BOYS_FUSED_MIN_BLOCKS 8
+#define BOYS_FUSED_MIN_BLOCKS 6
 #endif
 
 namespace boys {
@@ -59,20 +60,79 @@ __global__ void __launch_bounds__(kBlock, stored_min_blocks(KMAX)) k_eval_f64(co
         fp64::eval_store<KMAX, FULL_ROWS>(__ldcs(x + i), out + i, ld);
 }
 
-// out[i] = sum_k (-2 rho_i)^k F_k(x_i), by Horner in a = -2 rho from F_KMAX down.
+// |a|^E for a compile-time E >= 1, in the 64-bit-significand format (integer
+// pipes), by binary powering: about 2^-58 relative for E <= 17.
+template <int E>
+__device__ __forceinline__ xf::Xf xf_pow(xf::Xf b) {
+    xf::Xf r = b;
+    bool have = false;
+#pragma unroll
+    for (int bit = 0; (E >> bit) != 0; ++bit) {
+        if ((E >> bit) & 1) {
+            r = have ? xf::mul(r, b) : b;
+            have = true;
+        }
+        if ((E >> (bit + 1)) != 0) b = xf::mul(b, b);
+    }
+    return r;
+}
+
+// out[i] = sum_k a^k F_k(x_i), a = -2 rho_i, as two Horner sums in a that
+// follow the order in which the step loop completes the orders.  Step p
+// yields value p of the recurrence, F_{KMAX-p} on an A lane and F_p on a B or
+// C lane; as in stored mode, a lane holds its values p < KMAX/2, and each
+// later step p completes the pair F_q, F_p (q = KMAX - p) on every lane.
+//   low  = sum_{k <= KH} a^k F_k, KH = KMAX/2: the F_q arrive with q
+//          descending, so the Horner sum runs as they come;
+//   high = sum_{j < NH} a^j F_{KH+1+j}: the F_p arrive ascending, so each
+//          lane parks them in its own shared-memory column and sums them
+//          afterwards;
+//   out  = low + a^(KH+1) high, the power on the integer pipes.
+// The lane never keeps all kmax+1 values, so nothing spills; the FP64 work is
+// the KMAX FMAs of a single Horner sum plus one.
 template <int KMAX>
 __global__ void __launch_bounds__(kBlock, BOYS_FUSED_MIN_BLOCKS) k_fused_f64(const double* __restrict__ x,
                                                       const double* __restrict__ rho, int64_t n,
                                                       double* __restrict__ out) {
+    constexpr int KH = KMAX / 2;
+    constexpr int NH = KMAX - KH;
+    constexpr int NF = fused_fp64_steps(KMAX);
+    __shared__ double s_high[NH > 0 ? NH : 1][kBlock];
+    double* const park = &s_high[0][threadIdx.x];
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-        double F[KMAX + 1];
-        fp64::eval_point<KMAX, fused_fp64_steps(KMAX)>(__ldcs(x + i), F);
+        const fp64::Setup S = fp64::setup<KMAX, fp64::int_exp_for(KMAX, NF)>(__ldcs(x + i));
         const double a = -2.0 * __ldcs(rho + i);
-        double s = F[KMAX];
+        double hold[KH + 1];
+        double yd = S.y0d, low = 0.0;
+        xf::Xf y = S.y0;
 #pragma unroll
-        for (int k = KMAX - 1; k >= 0; --k) s = fma(s, a, F[k]);
-        __stcs(out + i, s);
+        for (int p = 0; p <= KMAX; ++p) {
+            const double v = fp64::next_value<KMAX, NF>(S, p, yd, y);
+            if (2 * p < KMAX) {
+                hold[p] = v;
+            } else if (2 * p == KMAX) {
+                low = v;                                    // F_KH on every lane
+            } else {
+                const int q = KMAX - p;
+                const double fq = S.inA ? v : hold[q];
+                low = (q == KH) ? fq : fma(low, a, fq);     // q == KH: the first low term (odd KMAX)
+                park[(p - KH - 1) * kBlock] = S.inA ? hold[q] : v;  // F_p
+            }
+        }
+        double r = low;
+        if (NH > 0) {
+            double high = park[(NH - 1) * kBlock];
+#pragma unroll
+            for (int j = NH - 2; j >= 0; --j) high = fma(high, a, park[j * kBlock]);
+            // a^(KH+1) from |a| on the integer pipes, with the sign of a^(KH+1)
+            const long long ab = __double_as_longlong(a);
+            const xf::Xf P = xf_pow<KH + 1>(xf::from_double(__longlong_as_double(ab & 0x7FFFFFFFFFFFFFFFLL)));
+            double w = P.e > 1023 ? __longlong_as_double(0x7FF0000000000000LL) : xf::to_double(P);
+            if (ab < 0 && ((KH + 1) & 1)) w = -w;
+            r = fma(w, high, low);
+        }
+        __stcs(out + i, r);
     }
 }
 

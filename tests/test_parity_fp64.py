@@ -161,6 +161,23 @@ def test_fused_against_oracle(kmax):
     assert np.all(err <= tol), f"kmax={kmax}: worst ratio {np.max(err / tol):.3f}"
 
 
+@pytest.mark.parametrize("kmax", [0, 1, 2, 15, 16, 17, 31, 32])
+def test_fused_rho_range(kmax):
+    """The two Horner sums and the power a^(kmax/2+1) that joins them, over
+    rho from 0 (the sum is F_0) and subnormal through 1e6, negative rho
+    (every term positive), on every region."""
+    rhos = np.array([0.0, 5e-324, 1e-300, 1e-20, 1e-3, 0.5, 3.0, 1e3, 1e6, -0.3, -40.0])
+    xs = np.array([0.0, 1e-9, 0.7, 5.0, 11.5, W.X0_PRINTED, 20.0, W.X1_PRINTED, 35.0, 1e4])
+    x = np.repeat(xs, rhos.size)
+    rho = np.tile(rhos, xs.size)
+    out = pb.boys_eval_fused(torch.from_numpy(x).to(DEV), torch.from_numpy(rho).to(DEV), kmax)
+    got = out.cpu().numpy()
+    hi, lo = oracle.fused(x, rho, kmax)
+    err = _err(got, hi, lo)
+    tol = _fused_tol(x, np.abs(rho), kmax)
+    assert np.all(err <= tol), f"kmax={kmax}: worst ratio {np.max(err / tol):.3f}"
+
+
 def test_fused_c2_full_size_sampled():
     n = 1 << 26
     x = W.mixture_c2(n, seed=1)
