@@ -125,10 +125,13 @@ __global__ void __launch_bounds__(kBlock, BOYS_FUSED_MIN_BLOCKS) k_fused_f64(con
             double high = park[(NH - 1) * kBlock];
 #pragma unroll
             for (int j = NH - 2; j >= 0; --j) high = fma(high, a, park[j * kBlock]);
-            // a^(KH+1) from |a| on the integer pipes, with the sign of a^(KH+1)
+            // a^(KH+1) from |a| on the integer pipes, with the sign of a^(KH+1);
+            // 0 for a zero or subnormal a (the format's zero must not be
+            // powered: its exponent would overflow)
             const long long ab = __double_as_longlong(a);
             const xf::Xf P = xf_pow<KH + 1>(xf::from_double(__longlong_as_double(ab & 0x7FFFFFFFFFFFFFFFLL)));
             double w = P.e > 1023 ? __longlong_as_double(0x7FF0000000000000LL) : xf::to_double(P);
+            if ((ab & 0x7FF0000000000000LL) == 0) w = 0.0;
             if (ab < 0 && ((KH + 1) & 1)) w = -w;
             r = fma(w, high, low);
         }
