@@ -233,7 +233,7 @@ boys_status boys_pairwise(const double* x, const double* y, int64_t n, const dou
  * or the argument count, so no call exceeds the array (the check is kept).
  *  * The first call on each device, with that device current, looks up the
  *    array's device address (cudaGetSymbolAddress, which may load the
- *    library's device code); make that first call before any stream capture.
+ *    library's device code).
  *  * Every call on a device shares the one array and re-zeroes its counter on
  *    `stream` first: calls that overlap on the GPU (other streams, other host
  *    threads) race with each other and produce wrong output.
