@@ -43,13 +43,14 @@ namespace fp64 {
 // sum) is the same at every kmax while the integer pipes take one step per
 // order, so the balance depends on kmax only (the kernels are branch-free, so
 // not on the argument mix).  Swept on GB300 (stored mode, N = 2^26, every kmax
-// x 0..22 FP64 steps, median of 3): with the denominator in FP64 (kmax <= 5
-// and 7) at most 2 steps; with both Horner sums on the integer pipes every
-// step up to kmax = 8, then about kmax / 2 + 1, 17 at kmax = 32 (4.69 ms,
-// against 6.33 with none and 4.81 with 14 or 5.16 with 20).
+// x 0..22 FP64 steps, median of 3, with the kernel's register caps and grid):
+// with the denominator in FP64 (kmax <= 5 and 7) at most 2 steps; with both
+// Horner sums on the integer pipes every step up to kmax = 8, then about
+// kmax / 2 + 1 up to kmax = 20 and fewer above, 15 at kmax = 32 (4.55 ms,
+// against 6.26 with none, 4.82 with 12, 4.59 with 17 and 5.04 with 20).
 // Defining BOYS_FP64_STEPS forces one value for every kmax.
-constexpr int kFp64Steps[33] = {0, 0, 0, 0, 2, 0, 6, 2, 8, 8, 8, 8, 9, 9, 10, 10, 10,
-                                11, 11, 11, 12, 12, 13, 13, 13, 13, 14, 14, 15, 15, 16, 16, 17};
+constexpr int kFp64Steps[33] = {0, 0, 0, 0, 2, 0, 6, 2, 8, 8, 8, 9, 9, 9, 10, 10, 11,
+                                11, 11, 12, 12, 11, 12, 12, 13, 14, 14, 14, 14, 14, 15, 16, 15};
 // The anchor's numerator p runs as a fixed-point Horner sum on the integer
 // pipes for kmax up to BOYS_FIXED_P_MAXK (-1: never), the denominator q in
 // FP64.  A fixed binary point serves the numerators (degree <= 8) to about
