@@ -61,8 +61,15 @@ __device__ __forceinline__ double w_region(const fp64::Setup& S, const double (&
     return w;
 }
 
+// Minimum resident blocks per SM (caps the registers): at the paper's N = 2^19,
+// x sorted, 8 blocks (64 registers) 6.98 s, 7 blocks 7.01, 9 7.06, 10 7.02,
+// the uncapped 76 registers 7.07.
+#ifndef BOYS_PAIRWISE_MIN_BLOCKS
+#define BOYS_PAIRWISE_MIN_BLOCKS 8
+#endif
+
 template <int K>
-__global__ void __launch_bounds__(kBlock) k_pairwise(const double* __restrict__ x, const double* __restrict__ y,
+__global__ void __launch_bounds__(kBlock, BOYS_PAIRWISE_MIN_BLOCKS) k_pairwise(const double* __restrict__ x, const double* __restrict__ y,
                                                      int64_t n, const double* __restrict__ c,
                                                      double* __restrict__ z) {
     __shared__ double sx[kBlock], sy[kBlock];
