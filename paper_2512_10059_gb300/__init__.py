@@ -5,5 +5,5 @@ declared in ``include/boys.h``); this package marshals torch CUDA tensors to
 it.  Nothing here computes Boys functions on the host.
 """
 from .api import (BoysFunction, RaggedPlan, boys, boys_eval, boys_eval_f32, boys_eval_fused,  # noqa: F401
-                  boys_eval_host, boys_eval_ragged, boys_pairwise,
-                  boys_grad, kmax_limit, ragged_layout, ragged_status, version)
+                  boys_eval_host, boys_eval_ragged, boys_eval_ragged_noalloc, boys_pairwise,
+                  boys_grad, kmax_limit, ragged_layout, ragged_noalloc_status, ragged_status, version)

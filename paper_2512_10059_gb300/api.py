@@ -233,6 +233,41 @@ def boys_eval_ragged(x, seg_off, seg_kmax, out=None, out_off=None, workspace=Non
     return out, out_off
 
 
+def boys_eval_ragged_noalloc(x, seg_off, seg_kmax, out=None, out_off=None, stream=None):
+    """The same batch as boys_eval_ragged through boys_eval_ragged_noalloc:
+    no workspace, and the library allocates nothing (its scratch is a static
+    array shared by every call on the device, so calls must not overlap on
+    the GPU).  ``out`` and ``out_off`` are created here only when not given.
+    Returns (out, out_off)."""
+    x, seg_off, seg_kmax = _ragged_args(x, seg_off, seg_kmax)
+    nseg = seg_kmax.numel()
+    if out_off is None:
+        out_off, total_out = ragged_layout(seg_off, seg_kmax)
+    else:
+        _require(out_off, "out_off", torch.int64)
+        total_out = None
+    if out is None:
+        if total_out is None:
+            raise ValueError("give out together with out_off")
+        out = torch.empty(max(total_out, 1), dtype=torch.float64, device=x.device)
+    _require(out, "out")
+    st = _lib.lib().boys_eval_ragged_noalloc(x.data_ptr(), seg_off.data_ptr(), seg_kmax.data_ptr(), nseg,
+                                             out.data_ptr(), out_off.data_ptr(), _stream_handle(x, stream))
+    _lib.check("boys_eval_ragged_noalloc", st)
+    return out, out_off
+
+
+def ragged_noalloc_status(device=None, stream=None) -> bool:
+    """True if the latest boys_eval_ragged_noalloc call on the current device
+    met a kmax outside [0, 32] (synchronises the stream)."""
+    with torch.cuda.device(device if device is not None else torch.cuda.current_device()):
+        hs = int(stream.cuda_stream) if stream is not None else int(torch.cuda.current_stream().cuda_stream)
+        flag = ctypes.c_int(0)
+        st = _lib.lib().boys_ragged_noalloc_status(ctypes.byref(flag), hs)
+    _lib.check("boys_ragged_noalloc_status", st)
+    return bool(flag.value)
+
+
 def ragged_status(workspace: torch.Tensor, stream=None) -> bool:
     """True if the last ragged launch on ``workspace`` met a kmax outside [0, 32]."""
     flag = ctypes.c_int(0)

@@ -104,3 +104,20 @@ def test_noalloc_reports_bad_kmax_and_clears_it():
                                       oo.data_ptr(), hs) == 0
     assert L.boys_ragged_noalloc_status(ctypes.byref(flag), hs) == 0
     assert flag.value == 0
+
+
+@pytest.mark.gpu
+def test_noalloc_python_binding():
+    """The binding's wrappers marshal to the same calls: bitwise the result
+    of boys_eval_ragged, and the status reads the error word."""
+    dev = "cuda:0"
+    x, off, kmax = _batch(34, 120)
+    xt = torch.from_numpy(x).to(dev)
+    ot = torch.from_numpy(off).to(dev)
+    kt = torch.from_numpy(kmax).to(dev)
+    ref, out_off = api.boys_eval_ragged(xt, ot, kt)
+    got, got_off = api.boys_eval_ragged_noalloc(xt, ot, kt)
+    assert torch.equal(got_off, out_off)
+    assert torch.equal(got, ref)
+    assert api.ragged_noalloc_status() is False
+
